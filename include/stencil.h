@@ -1,0 +1,168 @@
+/*
+ * stencil.h -- C ABI of the GB300 (sm_103a) library for iterated explicit 2D
+ * stencil sweeps.
+ *
+ * The operation (paper, Sec. II-C, the Jacobi update, and Sec. II-B for the
+ * Star / Box shapes of radius r):
+ *
+ *     u^{t+1}[i][j] = sum_{dy,dx in [-r, r]} W[dy+r][dx+r] * u~^{t}[i+dy][j+dx],
+ *     t = 0 .. T-1,
+ *
+ * on an ny x nx grid stored row-major (i = row, j = column, j contiguous).
+ * u~ extends u outside the grid: by zeros for STENCIL_BOUNDARY_ZERO (the
+ * paper's fixed zero padding, Sec. IV-A) or by wrapping for
+ * STENCIL_BOUNDARY_PERIODIC.  Every one of the ny*nx points is updated at every
+ * step; the zero halo is never updated.  W is a (2r+1)x(2r+1) row-major FP32
+ * array; entries off the footprint are 0.  The sum is a cross-correlation
+ * (no kernel flip).  All arithmetic is FP32 (FMA); the storage type of the
+ * grid in device memory may be FP32, BF16 or FP16 (rounded to nearest even on
+ * every store to device memory).
+ *
+ * Conventions for every entry point:
+ *   - Grid pointers are DEVICE pointers unless the name says _host.  The
+ *     caller owns them.  Rows are dense (row pitch = nx elements).
+ *   - Weights are HOST pointers and are copied; the caller may free them on return.
+ *   - Work is enqueued on `stream` (NULL = legacy default stream) and the call
+ *     returns without synchronising, except where stated.
+ *   - Errors: argument errors are reported synchronously and nothing is
+ *     enqueued.  A CUDA error becomes STENCIL_ERR_CUDA.  Device-side checks
+ *     (bounded waits that ran out, failed consistency checks) are recorded in
+ *     a status word that stencil_plan_status() / stencil_batch_status() read.
+ *     The library never traps and never aborts the process.
+ *   - stencil_last_error() returns a message for the last failure on the
+ *     calling thread.
+ *   - A plan (or batch) may be used by one stream at a time.
+ */
+#ifndef GB300_STENCIL_H
+#define GB300_STENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t, declared here so callers need no CUDA header. */
+typedef struct CUstream_st* stencil_stream_t;
+
+typedef enum {
+    STENCIL_OK = 0,
+    STENCIL_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum value        */
+    STENCIL_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. radius > 3)   */
+    STENCIL_ERR_CUDA = 3,          /* a CUDA runtime call failed                    */
+    STENCIL_ERR_OOM = 4,           /* device or host allocation failed              */
+    STENCIL_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out            */
+    STENCIL_ERR_DEVICE_CHECK = 6   /* a device-side consistency check failed        */
+} stencil_status_t;
+
+typedef enum { STENCIL_F32 = 0, STENCIL_BF16 = 1, STENCIL_F16 = 2 } stencil_dtype_t;
+
+typedef enum { STENCIL_BOUNDARY_ZERO = 0, STENCIL_BOUNDARY_PERIODIC = 1 } stencil_boundary_t;
+
+/* Arithmetic engine.  AUTO and FP32 use the CUDA cores; the tensor-core
+ * engines apply to the full 7x7 box (radius 3) only. */
+typedef enum {
+    STENCIL_COMPUTE_AUTO = 0,
+    STENCIL_COMPUTE_FP32 = 1,
+    STENCIL_COMPUTE_TC_TF32 = 2,
+    STENCIL_COMPUTE_TC_BF16 = 3
+} stencil_compute_t;
+
+/* Kernel family for the CUDA-core engine. */
+typedef enum {
+    STENCIL_KERNEL_AUTO = 0,
+    STENCIL_KERNEL_NAIVE = 1,      /* one thread per point, one step per launch      */
+    STENCIL_KERNEL_STREAM = 2      /* row-streaming tiles, k steps per launch        */
+} stencil_kernel_t;
+
+/* Optional plan settings; pass NULL for defaults.  0 means "choose". */
+typedef struct {
+    int compute;      /* stencil_compute_t                                          */
+    int kernel;       /* stencil_kernel_t                                           */
+    int tb_depth;     /* time steps per launch (temporal blocking depth k)          */
+    int threads;      /* threads per CTA of the streaming kernel (multiple of 32)   */
+    int tile_rows;    /* output rows per CTA tile of the streaming kernel           */
+    int autotune;     /* 1: time candidate configurations on first run              */
+} stencil_options_t;
+
+/* What a plan decided.  Filled by stencil_plan_info(). */
+typedef struct {
+    int64_t ny, nx;
+    int radius;
+    int shape;             /* 0 = general box, 1 = star (off-axis weights are 0)   */
+    int dtype, boundary, compute, kernel;
+    int tb_depth;          /* k                                                     */
+    int threads;           /* CTA size                                              */
+    int halo_cols;         /* halo columns loaded on each side of a strip          */
+    int tile_cols;         /* output columns per CTA                                */
+    int tile_rows;         /* output rows per CTA                                   */
+    int ctas;              /* CTAs per launch                                       */
+    int smem_bytes;        /* dynamic shared memory per CTA                         */
+    int64_t workspace_bytes;  /* device workspace the plan owns                    */
+} stencil_plan_info_t;
+
+typedef struct stencil_plan stencil_plan_t;
+
+/*
+ * Create a plan for T-step sweeps of one grid shape and weight set.
+ *   plan      out: the new plan (NULL on failure).
+ *   ny, nx    grid rows and columns, each >= 1.
+ *   radius    r in 1..3 (larger: STENCIL_ERR_UNSUPPORTED).
+ *   weights   HOST, (2r+1)^2 FP32, row-major, weights[(dy+r)*(2r+1)+(dx+r)]; copied.
+ *   dtype     stencil_dtype_t: storage type of grids in device memory.
+ *   boundary  stencil_boundary_t.
+ *   opt       NULL or settings.
+ * Allocates one grid-sized device workspace (ping-pong buffer) on the current device.
+ */
+stencil_status_t stencil_plan_create(stencil_plan_t** plan, int64_t ny, int64_t nx, int radius,
+                                     const float* weights, int dtype, int boundary,
+                                     const stencil_options_t* opt);
+
+/* Release a plan and its device workspace.  NULL is accepted. */
+void stencil_plan_destroy(stencil_plan_t* plan);
+
+/* Report the plan's choices (after stencil_plan_create; tuning may refine them on first run). */
+stencil_status_t stencil_plan_info(const stencil_plan_t* plan, stencil_plan_info_t* info);
+
+/*
+ * out = A^T in: T Jacobi steps (the paper's Sec. II-C update repeated, Sec. VI-A).
+ *   in, out   DEVICE grids of ny*nx elements of the plan's dtype.  `in` is only
+ *             read.  in == out is allowed.  Other partial overlap is an error
+ *             the library cannot detect.
+ *   T         >= 0.  T == 0 copies in to out.
+ * Launches ceil(T/k) kernels (k = tb_depth, +1 if in == out and that count is odd).
+ */
+stencil_status_t stencil_run(stencil_plan_t* plan, const void* in, void* out, int64_t T,
+                             stencil_stream_t stream);
+
+/*
+ * As stencil_run, with HOST input and output: copies in_host to a device buffer
+ * the plan owns, runs T steps, copies the result to out_host, and synchronises
+ * `stream` before returning.  Pinned host memory gives full copy bandwidth.
+ */
+stencil_status_t stencil_run_host(stencil_plan_t* plan, const void* in_host, void* out_host,
+                                  int64_t T, stencil_stream_t stream);
+
+/* Number of kernel launches stencil_run(plan, in, out, T) makes (in != out). */
+int64_t stencil_run_launches(const stencil_plan_t* plan, int64_t T);
+
+/*
+ * Synchronise the plan's last stream and read its device status word:
+ * STENCIL_OK, STENCIL_ERR_TIMEOUT or STENCIL_ERR_DEVICE_CHECK.  Clears the word.
+ */
+stencil_status_t stencil_plan_status(stencil_plan_t* plan);
+
+/* Human-readable name of a status code (static string). */
+const char* stencil_status_string(stencil_status_t status);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* stencil_last_error(void);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int stencil_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_STENCIL_H */

@@ -1,1 +1,125 @@
-"""GB300-native iterated explicit 2D stencil sweeps (sm_103a CUDA behind a C-ABI)."""
+"""GB300-native iterated explicit 2D stencil sweeps (sm_103a CUDA behind a C ABI).
+
+The computation (Jacobi update, paper Sec. II-C; zero padding as the boundary,
+Sec. IV-A) runs entirely in the CUDA library ``libstencil_gb300.so``; this
+package only marshals arguments.  PyTorch supplies device memory and the
+current stream.  ``_capi`` holds the raw C entry points under their C names;
+:class:`Plan` is a thin convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import StencilError, check
+
+DTYPES = {"f32": _capi.STENCIL_F32, "bf16": _capi.STENCIL_BF16, "f16": _capi.STENCIL_F16}
+BOUNDARIES = {"zero": _capi.STENCIL_BOUNDARY_ZERO, "periodic": _capi.STENCIL_BOUNDARY_PERIODIC}
+COMPUTES = {"auto": 0, "fp32": 1, "tc_tf32": 2, "tc_bf16": 3}
+KERNELS = {"auto": 0, "naive": 1, "stream": 2}
+
+
+def _torch_dtype_name(t) -> str:
+    import torch
+    return {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16"}[t]
+
+
+def _current_stream_handle() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """A plan for T-step sweeps of one (ny, nx) grid with one weight set."""
+
+    def __init__(self, ny: int, nx: int, weights, dtype: str = "f32", boundary: str = "zero",
+                 compute: str = "auto", kernel: str = "auto", tb_depth: int = 0,
+                 threads: int = 0, tile_rows: int = 0, autotune: bool = False):
+        lib = _capi.load()
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+        d = w.shape[0]
+        if w.ndim != 2 or w.shape[1] != d or d % 2 != 1:
+            raise ValueError(f"weights must be (2r+1, 2r+1), got {w.shape}")
+        self.radius = d // 2
+        self.shape = (int(ny), int(nx))
+        self.dtype = dtype
+        self.weights = w
+        opt = _capi.stencil_options_t(COMPUTES[compute], KERNELS[kernel], int(tb_depth),
+                                      int(threads), int(tile_rows), int(bool(autotune)))
+        h = ctypes.c_void_p()
+        check(lib.stencil_plan_create(ctypes.byref(h), int(ny), int(nx), self.radius,
+                                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                      DTYPES[dtype], BOUNDARIES[boundary], ctypes.byref(opt)),
+              "stencil_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _capi.load().stencil_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = _capi.stencil_plan_info_t()
+        check(_capi.load().stencil_plan_info(self._h, ctypes.byref(i)), "stencil_plan_info")
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def launches(self, T: int) -> int:
+        return int(_capi.load().stencil_run_launches(self._h, int(T)))
+
+    def _check_tensor(self, x):
+        import torch
+        if not x.is_cuda or not x.is_contiguous() or tuple(x.shape) != self.shape:
+            raise ValueError(f"expected a contiguous CUDA tensor of shape {self.shape}")
+        if _torch_dtype_name(x.dtype) != self.dtype:
+            raise ValueError(f"expected dtype {self.dtype}, got {x.dtype}")
+        return torch
+
+    def run(self, x, T: int, out=None):
+        """u_T from u_0 = x (device tensor); enqueued on torch's current stream."""
+        torch = self._check_tensor(x)
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            self._check_tensor(out)
+        check(_capi.load().stencil_run(self._h, x.data_ptr(), out.data_ptr(), int(T),
+                                       _current_stream_handle()), "stencil_run")
+        return out
+
+    def run_host(self, x: np.ndarray, T: int, out: np.ndarray | None = None, stream: int = 0):
+        """Host in, host out: H2D copy, T steps and D2H copy, synchronised."""
+        if x.shape != self.shape or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"expected a C-contiguous array of shape {self.shape}")
+        if out is None:
+            out = np.empty_like(x)
+        check(_capi.load().stencil_run_host(self._h, x.ctypes.data, out.ctypes.data, int(T),
+                                            stream), "stencil_run_host")
+        return out
+
+    def status(self):
+        check(_capi.load().stencil_plan_status(self._h), "stencil_plan_status")
+
+
+def run(x, weights, T: int, boundary: str = "zero", **options):
+    """One-shot convenience: plan, run on the current stream, return u_T."""
+    p = Plan(x.shape[0], x.shape[1], weights, dtype=_torch_dtype_name(x.dtype),
+             boundary=boundary, **options)
+    y = p.run(x, T)
+    import torch
+    torch.cuda.current_stream().synchronize()
+    p.close()
+    return y
+
+
+__all__ = ["Plan", "run", "StencilError", "DTYPES", "BOUNDARIES"]

@@ -1,0 +1,429 @@
+// plan.cu -- host side of the C ABI: plans, launch sequencing, workspace.
+//
+// A plan fixes (shape, radius, weights, dtype, boundary) and picks a kernel
+// configuration: the temporal-blocking depth k, the CTA size and the tile
+// shape of the streaming kernel (sweep_stream.cuh), or the naive kernel.
+// stencil_run() then issues ceil(T/k) launches that ping-pong between the
+// caller's output and one plan-owned workspace grid, so that the last launch
+// writes `out` and `in` is never written.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "common.cuh"
+#include "sweep_stream.cuh"
+
+namespace gbst {
+StreamKernelRef get_stream_kernel_r1(int star, int kmin, int dtype);
+StreamKernelRef get_stream_kernel_r2(int star, int kmin, int dtype);
+StreamKernelRef get_stream_kernel_r3(int star, int kmin, int dtype);
+int stream_kmax_r1();
+int stream_kmax_r2();
+int stream_kmax_r3();
+const void* get_naive_kernel(int radius, int dtype);
+}  // namespace gbst
+
+using namespace gbst;
+
+static thread_local std::string g_last_error;
+
+static stencil_status_t fail(stencil_status_t st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            return fail(STENCIL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                            \
+    } while (0)
+
+struct stencil_plan {
+    int64_t ny = 0, nx = 0;
+    int R = 0;
+    int star = 0;
+    int dtype = 0, boundary = 0, compute = 0;
+    Weights w{};
+    stencil_options_t opt{};
+    int device = 0, sms = 0;
+    // chosen configuration
+    int kernel = STENCIL_KERNEL_STREAM;
+    int k = 1, threads = 0, H = 0, bx = 0, by = 0, strips = 0, tiles_y = 0, smem = 0;
+    StreamKernelRef sk{nullptr, 0};
+    const void* naive = nullptr;
+    // memory
+    size_t elem = 4;
+    void* ws = nullptr;
+    void* host_in = nullptr;
+    void* host_out = nullptr;
+    unsigned int* status = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+static size_t elem_size(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static StreamKernelRef stream_kernel(int R, int star, int kmin, int dtype) {
+    switch (R) {
+        case 1: return get_stream_kernel_r1(star, kmin, dtype);
+        case 2: return get_stream_kernel_r2(star, kmin, dtype);
+        case 3: return get_stream_kernel_r3(star, kmin, dtype);
+        default: return {nullptr, 0};
+    }
+}
+
+static int stream_kmax(int R) {
+    switch (R) {
+        case 1: return stream_kmax_r1();
+        case 2: return stream_kmax_r2();
+        case 3: return stream_kmax_r3();
+        default: return 0;
+    }
+}
+
+// Default depth before any tuning: deep enough that HBM stops binding for the
+// light stencils, 1 for the 49-point box (already arithmetic-bound at k = 1).
+static int default_depth(int R, int star) {
+    if (R == 1) return 8;
+    if (R == 2) return 4;
+    return star ? 4 : 1;
+}
+
+// Fill the streaming kernel's tile configuration for depth k and CTA size threads.
+static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, int tile_rows) {
+    const int kmax = stream_kmax(p->R);
+    if (k < 1 || k > kmax)
+        return fail(STENCIL_ERR_UNSUPPORTED,
+                    "tb_depth " + std::to_string(k) + " outside 1.." + std::to_string(kmax) +
+                        " for radius " + std::to_string(p->R));
+    if (threads < 32 || threads > 256 || threads % 32)
+        return fail(STENCIL_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..256");
+    StreamKernelRef sk = stream_kernel(p->R, p->star, k, p->dtype);
+    if (!sk.fn) return fail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for this radius/depth");
+    const int H = (p->R * k + 3) / 4 * 4;
+    const int bx_max = 4 * threads - 2 * H;
+    if (bx_max < 4) return fail(STENCIL_ERR_UNSUPPORTED, "CTA too narrow for this depth");
+    const int64_t strips = ceil_div(p->nx, bx_max);
+    const int bx = (int)(ceil_div(ceil_div(p->nx, strips), 4) * 4);
+    const int nt = (int)(ceil_div(ceil_div(bx + 2 * H, 4), 32) * 32);
+    const int smem = 2 * sk.kmax * (4 * nt + 8) * 4;
+    CK(cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, nt, smem));
+    if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "streaming kernel does not fit on an SM");
+    int64_t tiles_y;
+    int by;
+    if (tile_rows > 0) {
+        by = tile_rows;
+        tiles_y = ceil_div(p->ny, by);
+    } else {
+        const int64_t resident = (int64_t)per_sm * p->sms;
+        const int64_t by_min = std::max<int64_t>(8, 4LL * p->R * k);
+        const int64_t want = std::max<int64_t>(1, resident / strips);
+        tiles_y = std::max<int64_t>(1, std::min<int64_t>(want, ceil_div(p->ny, by_min)));
+        by = (int)ceil_div(p->ny, tiles_y);
+        tiles_y = ceil_div(p->ny, by);
+    }
+    if (strips * tiles_y > 0x7fffffffLL) return fail(STENCIL_ERR_UNSUPPORTED, "grid too large");
+    p->kernel = STENCIL_KERNEL_STREAM;
+    p->k = k;
+    p->threads = nt;
+    p->H = H;
+    p->bx = bx;
+    p->by = by;
+    p->strips = (int)strips;
+    p->tiles_y = (int)tiles_y;
+    p->smem = smem;
+    p->sk = sk;
+    return STENCIL_OK;
+}
+
+static stencil_status_t configure_naive(stencil_plan* p) {
+    p->naive = get_naive_kernel(p->R, p->dtype);
+    if (!p->naive) return fail(STENCIL_ERR_UNSUPPORTED, "no naive kernel for this radius");
+    p->kernel = STENCIL_KERNEL_NAIVE;
+    p->k = 1;
+    p->threads = 256;
+    p->H = 0;
+    p->bx = 32;
+    p->by = 8;
+    p->strips = (int)ceil_div(p->nx, 32);
+    p->tiles_y = (int)std::min<int64_t>(ceil_div(p->ny, 8), 65535);
+    p->smem = 0;
+    return STENCIL_OK;
+}
+
+// One launch advancing `nlev` steps from src to dst.
+static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst, int nlev,
+                                    cudaStream_t st) {
+    if (p->kernel == STENCIL_KERNEL_NAIVE) {
+        dim3 block(32, 8), grid((unsigned)p->strips, (unsigned)p->tiles_y);
+        long long ny = p->ny, nx = p->nx;
+        int periodic = p->boundary;
+        void* args[] = {(void*)&src, (void*)&dst, &ny, &nx, &periodic, &p->w};
+        CK(cudaLaunchKernel(p->naive, grid, block, args, 0, st));
+        return STENCIL_OK;
+    }
+    StreamParams sp{};
+    sp.in = src;
+    sp.out = dst;
+    sp.ny = p->ny;
+    sp.nx = p->nx;
+    sp.nlev = nlev;
+    sp.H = p->H;
+    sp.bx = p->bx;
+    sp.by = p->by;
+    sp.strips = p->strips;
+    sp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+    const size_t row_bytes = (size_t)p->nx * p->elem;
+    const size_t vec_bytes = 4 * p->elem;
+    sp.vec = (p->nx % 4 == 0) && ((uintptr_t)src % vec_bytes == 0) &&
+             ((uintptr_t)dst % vec_bytes == 0) && (row_bytes % vec_bytes == 0);
+    sp.w = p->w;
+    void* args[] = {&sp};
+    dim3 grid((unsigned)(p->strips * p->tiles_y)), block((unsigned)p->threads);
+    CK(cudaLaunchKernel(p->sk.fn, grid, block, args, (size_t)p->smem, st));
+    return STENCIL_OK;
+}
+
+// Depths of the launches for T steps: full blocks of k, then the remainder.
+static std::vector<int> launch_depths(const stencil_plan* p, int64_t T) {
+    std::vector<int> d;
+    const int k = p->kernel == STENCIL_KERNEL_NAIVE ? 1 : p->k;
+    for (int64_t t = 0; t < T / k; ++t) d.push_back(k);
+    if (T % k) d.push_back((int)(T % k));
+    return d;
+}
+
+extern "C" {
+
+const char* stencil_status_string(stencil_status_t s) {
+    switch (s) {
+        case STENCIL_OK: return "STENCIL_OK";
+        case STENCIL_ERR_INVALID_ARG: return "STENCIL_ERR_INVALID_ARG";
+        case STENCIL_ERR_UNSUPPORTED: return "STENCIL_ERR_UNSUPPORTED";
+        case STENCIL_ERR_CUDA: return "STENCIL_ERR_CUDA";
+        case STENCIL_ERR_OOM: return "STENCIL_ERR_OOM";
+        case STENCIL_ERR_TIMEOUT: return "STENCIL_ERR_TIMEOUT";
+        case STENCIL_ERR_DEVICE_CHECK: return "STENCIL_ERR_DEVICE_CHECK";
+        default: return "STENCIL_ERR_UNKNOWN";
+    }
+}
+
+const char* stencil_last_error(void) { return g_last_error.c_str(); }
+
+int stencil_version(void) { return 100; }
+
+stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t nx, int radius,
+                                     const float* weights, int dtype, int boundary,
+                                     const stencil_options_t* opt) {
+    if (!out) return fail(STENCIL_ERR_INVALID_ARG, "plan pointer is NULL");
+    *out = nullptr;
+    if (ny < 1 || nx < 1) return fail(STENCIL_ERR_INVALID_ARG, "ny and nx must be >= 1");
+    if (radius < 1) return fail(STENCIL_ERR_INVALID_ARG, "radius must be >= 1");
+    if (radius > kMaxRadius) return fail(STENCIL_ERR_UNSUPPORTED, "radius > 3 is not supported");
+    if (!weights) return fail(STENCIL_ERR_INVALID_ARG, "weights pointer is NULL");
+    if (dtype < STENCIL_F32 || dtype > STENCIL_F16) return fail(STENCIL_ERR_INVALID_ARG, "bad dtype");
+    if (boundary != STENCIL_BOUNDARY_ZERO && boundary != STENCIL_BOUNDARY_PERIODIC)
+        return fail(STENCIL_ERR_INVALID_ARG, "bad boundary");
+    stencil_options_t o{};
+    if (opt) o = *opt;
+    if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_BF16 || o.kernel < 0 ||
+        o.kernel > STENCIL_KERNEL_STREAM || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0)
+        return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
+    if (o.compute == STENCIL_COMPUTE_TC_TF32 || o.compute == STENCIL_COMPUTE_TC_BF16)
+        return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engine not available in this build");
+
+    stencil_plan* p = new (std::nothrow) stencil_plan();
+    if (!p) return fail(STENCIL_ERR_OOM, "host allocation failed");
+    p->ny = ny;
+    p->nx = nx;
+    p->R = radius;
+    p->dtype = dtype;
+    p->boundary = boundary;
+    p->compute = STENCIL_COMPUTE_FP32;
+    p->opt = o;
+    p->elem = elem_size(dtype);
+    const int D = 2 * radius + 1;
+    int star = 1;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            const float v = weights[a * D + b];
+            if (!std::isfinite(v)) {
+                delete p;
+                return fail(STENCIL_ERR_INVALID_ARG, "weights must be finite");
+            }
+            p->w.w[a * D + b] = v;
+            if (a != radius && b != radius && v != 0.f) star = 0;
+        }
+    p->star = star;
+
+    auto bail = [&](stencil_status_t st) {
+        stencil_plan_destroy(p);
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(STENCIL_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(STENCIL_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    }
+
+    stencil_status_t st;
+    if (o.kernel == STENCIL_KERNEL_NAIVE) {
+        st = configure_naive(p);
+    } else {
+        const int k = o.tb_depth > 0 ? o.tb_depth : default_depth(radius, star);
+        const int threads = o.threads > 0 ? o.threads : (k >= 8 ? 128 : 256);
+        st = configure_stream(p, std::min(k, stream_kmax(radius)), threads, o.tile_rows);
+    }
+    if (st != STENCIL_OK) return bail(st);
+
+    const size_t bytes = (size_t)ny * (size_t)nx * p->elem;
+    e = cudaMalloc(&p->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p->ws = nullptr;
+        bail(STENCIL_ERR_OOM);
+        return fail(STENCIL_ERR_OOM, "cudaMalloc of the workspace failed");
+    }
+    e = cudaMalloc(&p->status, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bail(STENCIL_ERR_OOM);
+        return fail(STENCIL_ERR_OOM, "cudaMalloc of the status word failed");
+    }
+    *out = p;
+    return STENCIL_OK;
+}
+
+void stencil_plan_destroy(stencil_plan_t* p) {
+    if (!p) return;
+    if (p->ws) cudaFree(p->ws);
+    if (p->host_in) cudaFree(p->host_in);
+    if (p->host_out) cudaFree(p->host_out);
+    if (p->status) cudaFree(p->status);
+    delete p;
+}
+
+stencil_status_t stencil_plan_info(const stencil_plan_t* p, stencil_plan_info_t* info) {
+    if (!p || !info) return fail(STENCIL_ERR_INVALID_ARG, "NULL argument");
+    stencil_plan_info_t i{};
+    i.ny = p->ny;
+    i.nx = p->nx;
+    i.radius = p->R;
+    i.shape = p->star;
+    i.dtype = p->dtype;
+    i.boundary = p->boundary;
+    i.compute = p->compute;
+    i.kernel = p->kernel;
+    i.tb_depth = p->k;
+    i.threads = p->threads;
+    i.halo_cols = p->H;
+    i.tile_cols = p->bx;
+    i.tile_rows = p->by;
+    i.ctas = p->strips * p->tiles_y;
+    i.smem_bytes = p->smem;
+    i.workspace_bytes = (int64_t)((size_t)p->ny * p->nx * p->elem);
+    *info = i;
+    return STENCIL_OK;
+}
+
+int64_t stencil_run_launches(const stencil_plan_t* p, int64_t T) {
+    if (!p || T < 0) return -1;
+    return (int64_t)launch_depths(p, T).size();
+}
+
+stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64_t T,
+                             stencil_stream_t stream) {
+    if (!p) return fail(STENCIL_ERR_INVALID_ARG, "plan is NULL");
+    if (!in || !out) return fail(STENCIL_ERR_INVALID_ARG, "in/out is NULL");
+    if (T < 0) return fail(STENCIL_ERR_INVALID_ARG, "T must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    p->last_stream = st;
+    const size_t bytes = (size_t)p->ny * p->nx * p->elem;
+    if (T == 0) {
+        if (in != out) CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
+        return STENCIL_OK;
+    }
+    std::vector<int> depths = launch_depths(p, T);
+    const void* src = in;
+    if (in == out && depths.size() % 2 == 1) {
+        // An odd launch count would make launch 1 write the grid it reads.
+        // Split one launch in two when possible, else stage the input.
+        auto it = std::find_if(depths.begin(), depths.end(), [](int d) { return d >= 2; });
+        if (it != depths.end()) {
+            const int d = *it;
+            *it = d / 2;
+            depths.insert(it, d - d / 2);
+        } else {
+            CK(cudaMemcpyAsync(p->ws, in, bytes, cudaMemcpyDeviceToDevice, st));
+            src = p->ws;
+        }
+    }
+    const size_t L = depths.size();
+    for (size_t i = 0; i < L; ++i) {
+        // Launch i (0-based) writes `out` when L-1-i is even, else the workspace.
+        void* dst = ((L - 1 - i) % 2 == 0) ? out : p->ws;
+        stencil_status_t s = launch_once(p, src, dst, depths[i], st);
+        if (s != STENCIL_OK) return s;
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_run_host(stencil_plan_t* p, const void* in_host, void* out_host,
+                                  int64_t T, stencil_stream_t stream) {
+    if (!p) return fail(STENCIL_ERR_INVALID_ARG, "plan is NULL");
+    if (!in_host || !out_host) return fail(STENCIL_ERR_INVALID_ARG, "in/out is NULL");
+    if (T < 0) return fail(STENCIL_ERR_INVALID_ARG, "T must be >= 0");
+    const size_t bytes = (size_t)p->ny * p->nx * p->elem;
+    if (!p->host_in) {
+        if (cudaMalloc(&p->host_in, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p->host_in = nullptr;
+            return fail(STENCIL_ERR_OOM, "cudaMalloc of the staging input failed");
+        }
+    }
+    if (!p->host_out) {
+        if (cudaMalloc(&p->host_out, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p->host_out = nullptr;
+            return fail(STENCIL_ERR_OOM, "cudaMalloc of the staging output failed");
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(p->host_in, in_host, bytes, cudaMemcpyHostToDevice, st));
+    stencil_status_t s = stencil_run(p, p->host_in, p->host_out, T, stream);
+    if (s != STENCIL_OK) return s;
+    CK(cudaMemcpyAsync(out_host, p->host_out, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_plan_status(stencil_plan_t* p) {
+    if (!p) return fail(STENCIL_ERR_INVALID_ARG, "plan is NULL");
+    CK(cudaStreamSynchronize(p->last_stream));
+    unsigned int word = 0;
+    CK(cudaMemcpy(&word, p->status, sizeof(word), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(p->status, 0, sizeof(word)));
+    if (word == 0) return STENCIL_OK;
+    return word == STENCIL_ERR_TIMEOUT ? STENCIL_ERR_TIMEOUT : STENCIL_ERR_DEVICE_CHECK;
+}
+
+}  // extern "C"

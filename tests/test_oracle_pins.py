@@ -123,9 +123,13 @@ def test_dyadic_exact(oracle, r, T):
     want = np.array([[float(v) / scale for v in row] for row in exact])
     got = oracle.sweep_f64(ui / 256.0, Wi / 8.0, T)
     assert np.array_equal(got, want)
-    if r == 1 and T <= 4:
-        got32 = oracle.sweep_f32((ui / 256.0).astype(np.float32), (Wi / 8.0).astype(np.float32), T)
-        assert np.array_equal(got32.astype(np.float64), want)
+    # FP32 is exact while |numerator| <= (2 * 9)^T * 255 < 2^24, i.e. T <= 3 at r = 1.
+    if r == 1:
+        T3 = 3
+        exact3 = _int_sweep(ui, Wi, T3, r)
+        want3 = np.array([[float(v) / (8 ** T3 * 256) for v in row] for row in exact3])
+        got32 = oracle.sweep_f32((ui / 256.0).astype(np.float32), (Wi / 8.0).astype(np.float32), T3)
+        assert np.array_equal(got32.astype(np.float64), want3)
 
 
 @pytest.mark.parametrize("name", ["heat5", "box9", "star13", "box49", "asym"])
