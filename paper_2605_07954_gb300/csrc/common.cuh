@@ -20,6 +20,12 @@ struct Weights {
     float w[kMaxTaps];
 };
 
+// The same weights duplicated into (w, w) pairs: the packed FP32x2 FMAs take a
+// pair straight from the constant bank instead of building it in registers.
+struct WeightPairs {
+    float2 w2[kMaxTaps];
+};
+
 // Parameters of the row-streaming kernel (see sweep_stream.cuh).
 struct StreamParams {
     const void* in;
@@ -33,6 +39,7 @@ struct StreamParams {
     int periodic;  // 1: wrap indices; 0: zero outside the grid
     int vec;       // 1: rows 16-byte aligned for 4-element vector access
     Weights w;
+    WeightPairs w2;
 };
 
 // ---- storage <-> FP32 ---------------------------------------------------------------

@@ -13,20 +13,23 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/stencil.h"
 #include "common.cuh"
+#include "stream_depths.h"
 #include "sweep_stream.cuh"
 
 namespace gbst {
-StreamKernelRef get_stream_kernel_r1(int star, int kmin, int dtype);
-StreamKernelRef get_stream_kernel_r2(int star, int kmin, int dtype);
-StreamKernelRef get_stream_kernel_r3(int star, int kmin, int dtype);
-int stream_kmax_r1();
-int stream_kmax_r2();
-int stream_kmax_r3();
+#define GBST_DECL_STREAM(R, DT) StreamKernelRef get_stream_kernel_r##R##_##DT(int star, int k, int vec);
+GBST_DECL_STREAM(1, f32) GBST_DECL_STREAM(1, bf16) GBST_DECL_STREAM(1, f16)
+GBST_DECL_STREAM(2, f32) GBST_DECL_STREAM(2, bf16) GBST_DECL_STREAM(2, f16)
+GBST_DECL_STREAM(3, f32) GBST_DECL_STREAM(3, bf16) GBST_DECL_STREAM(3, f16)
+#undef GBST_DECL_STREAM
 const void* get_naive_kernel(int radius, int dtype);
 }  // namespace gbst
 
@@ -58,7 +61,9 @@ struct stencil_plan {
     // chosen configuration
     int kernel = STENCIL_KERNEL_STREAM;
     int k = 1, threads = 0, H = 0, bx = 0, by = 0, strips = 0, tiles_y = 0, smem = 0;
-    StreamKernelRef sk{nullptr, 0};
+    int per_sm = 0;
+    unsigned smem_set = 0;  // bit 2k+vec: that kernel's shared-memory attribute is set
+    int tuned = 0;
     const void* naive = nullptr;
     // memory
     size_t elem = 4;
@@ -73,53 +78,79 @@ static size_t elem_size(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-static StreamKernelRef stream_kernel(int R, int star, int kmin, int dtype) {
-    switch (R) {
-        case 1: return get_stream_kernel_r1(star, kmin, dtype);
-        case 2: return get_stream_kernel_r2(star, kmin, dtype);
-        case 3: return get_stream_kernel_r3(star, kmin, dtype);
-        default: return {nullptr, 0};
-    }
+static StreamKernelRef stream_kernel(int R, int star, int k, int dtype, int vec) {
+    typedef StreamKernelRef (*Getter)(int, int, int);
+    static const Getter table[3][3] = {
+        {get_stream_kernel_r1_f32, get_stream_kernel_r1_bf16, get_stream_kernel_r1_f16},
+        {get_stream_kernel_r2_f32, get_stream_kernel_r2_bf16, get_stream_kernel_r2_f16},
+        {get_stream_kernel_r3_f32, get_stream_kernel_r3_bf16, get_stream_kernel_r3_f16}};
+    if (R < 1 || R > 3 || dtype < 0 || dtype > 2) return {nullptr, 0};
+    return table[R - 1][dtype](star, k, vec);
 }
 
-static int stream_kmax(int R) {
-    switch (R) {
-        case 1: return stream_kmax_r1();
-        case 2: return stream_kmax_r2();
-        case 3: return stream_kmax_r3();
-        default: return 0;
-    }
+// Largest instantiated depth for (R, star), and the largest one <= k.
+static int stream_kmax(int R, int star) {
+    int m = 0;
+    for (int i = 0; i < 8 && kStreamDepths[R - 1][star][i]; ++i) m = kStreamDepths[R - 1][star][i];
+    return m;
+}
+
+static int stream_depth_at_most(int R, int star, int k) {
+    int m = 0;
+    for (int i = 0; i < 8 && kStreamDepths[R - 1][star][i]; ++i)
+        if (kStreamDepths[R - 1][star][i] <= k) m = kStreamDepths[R - 1][star][i];
+    return m;
 }
 
 // Default depth before any tuning: deep enough that HBM stops binding for the
 // light stencils, 1 for the 49-point box (already arithmetic-bound at k = 1).
+// These are the best measured choices for 8192^2 FP32 grids on GB300.
 static int default_depth(int R, int star) {
     if (R == 1) return 8;
     if (R == 2) return 4;
     return star ? 4 : 1;
 }
 
+static const int kDefaultThreads = 128;
+
+// The depth-`depth` streaming kernel (VEC or element-wise variant), with its
+// shared-memory attribute set on first use.
+static stencil_status_t stream_fn(stencil_plan* p, int depth, int vec, const void** fn, int* smem) {
+    StreamKernelRef r = stream_kernel(p->R, p->star, depth, p->dtype, vec);
+    if (!r.fn) return fail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for depth " + std::to_string(depth));
+    *smem = stream_smem_bytes(p->R, depth, (int)p->elem, vec != 0);
+    const unsigned bit = 1u << (2 * depth + (vec ? 1 : 0));
+    if (!(p->smem_set & bit)) {
+        CK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
+        p->smem_set |= bit;
+    }
+    *fn = r.fn;
+    return STENCIL_OK;
+}
+
 // Fill the streaming kernel's tile configuration for depth k and CTA size threads.
 static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, int tile_rows) {
-    const int kmax = stream_kmax(p->R);
+    const int kmax = stream_kmax(p->R, p->star);
     if (k < 1 || k > kmax)
         return fail(STENCIL_ERR_UNSUPPORTED,
                     "tb_depth " + std::to_string(k) + " outside 1.." + std::to_string(kmax) +
                         " for radius " + std::to_string(p->R));
-    if (threads < 32 || threads > 256 || threads % 32)
+    k = stream_depth_at_most(p->R, p->star, k);
+    if (threads < 32 || threads > kStreamMaxThreads || threads % 32)
         return fail(STENCIL_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..256");
-    StreamKernelRef sk = stream_kernel(p->R, p->star, k, p->dtype);
-    if (!sk.fn) return fail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for this radius/depth");
+    const int vec = p->nx % 4 == 0;
+    const void* fn = nullptr;
+    int smem = 0;
+    stencil_status_t st = stream_fn(p, k, vec, &fn, &smem);
+    if (st != STENCIL_OK) return st;
     const int H = (p->R * k + 3) / 4 * 4;
     const int bx_max = 4 * threads - 2 * H;
     if (bx_max < 4) return fail(STENCIL_ERR_UNSUPPORTED, "CTA too narrow for this depth");
     const int64_t strips = ceil_div(p->nx, bx_max);
     const int bx = (int)(ceil_div(ceil_div(p->nx, strips), 4) * 4);
     const int nt = (int)(ceil_div(ceil_div(bx + 2 * H, 4), 32) * 32);
-    const int smem = 2 * sk.kmax * (4 * nt + 8) * 4;
-    CK(cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, nt, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
     if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "streaming kernel does not fit on an SM");
     int64_t tiles_y;
     int by;
@@ -144,7 +175,7 @@ static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, in
     p->strips = (int)strips;
     p->tiles_y = (int)tiles_y;
     p->smem = smem;
-    p->sk = sk;
+    p->per_sm = per_sm;
     return STENCIL_OK;
 }
 
@@ -185,24 +216,105 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
     sp.by = p->by;
     sp.strips = p->strips;
     sp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
-    const size_t row_bytes = (size_t)p->nx * p->elem;
     const size_t vec_bytes = 4 * p->elem;
     sp.vec = (p->nx % 4 == 0) && ((uintptr_t)src % vec_bytes == 0) &&
-             ((uintptr_t)dst % vec_bytes == 0) && (row_bytes % vec_bytes == 0);
+             ((uintptr_t)dst % vec_bytes == 0);
     sp.w = p->w;
+    for (int i = 0; i < kMaxTaps; ++i) sp.w2.w2[i] = make_float2(p->w.w[i], p->w.w[i]);
+    const void* fn = nullptr;
+    int smem = 0;
+    stencil_status_t s = stream_fn(p, nlev, sp.vec, &fn, &smem);
+    if (s != STENCIL_OK) return s;
     void* args[] = {&sp};
     dim3 grid((unsigned)(p->strips * p->tiles_y)), block((unsigned)p->threads);
-    CK(cudaLaunchKernel(p->sk.fn, grid, block, args, (size_t)p->smem, st));
+    CK(cudaLaunchKernel(fn, grid, block, args, (size_t)smem, st));
     return STENCIL_OK;
 }
 
-// Depths of the launches for T steps: full blocks of k, then the remainder.
+// Depths of the launches for T steps: full blocks of k, then the remainder
+// split greedily into instantiated depths.
 static std::vector<int> launch_depths(const stencil_plan* p, int64_t T) {
     std::vector<int> d;
     const int k = p->kernel == STENCIL_KERNEL_NAIVE ? 1 : p->k;
     for (int64_t t = 0; t < T / k; ++t) d.push_back(k);
-    if (T % k) d.push_back((int)(T % k));
+    int rem = (int)(T % k);
+    while (rem > 0) {
+        const int step = p->kernel == STENCIL_KERNEL_NAIVE ? 1 : stream_depth_at_most(p->R, p->star, rem);
+        d.push_back(step);
+        rem -= step;
+    }
     return d;
+}
+
+// ---- autotuning ---------------------------------------------------------------------
+//
+// With opt.autotune, the first stencil_run times every instantiated depth k
+// with CTAs of 64, 128 and 256 threads (the depth and CTA size the caller
+// fixed, if any, stay fixed) and keeps the fastest per step.  Each candidate
+// runs one launch from `in` into the plan's workspace, so neither `in` nor
+// `out` is touched.  Results are cached per (shape, radius, footprint, dtype,
+// boundary, device) for the life of the process.
+
+typedef std::tuple<int64_t, int64_t, int, int, int, int, int> TuneKey;
+static std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+static std::mutex g_tune_mu;
+
+static stencil_status_t time_launch(stencil_plan* p, const void* in, int reps, cudaStream_t st,
+                                    float* ms) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    stencil_status_t s = launch_once(p, in, p->ws, p->k, st);  // warm-up
+    if (s == STENCIL_OK) {
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < reps && s == STENCIL_OK; ++i) s = launch_once(p, in, p->ws, p->k, st);
+        cudaEventRecord(e1, st);
+    }
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (s == STENCIL_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != STENCIL_OK) return s;
+    if (e != cudaSuccess) return fail(STENCIL_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+    return STENCIL_OK;
+}
+
+static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t st) {
+    const TuneKey key(p->ny, p->nx, p->R, p->star, p->dtype, p->boundary, p->device);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end())
+            return configure_stream(p, it->second.first, it->second.second, p->opt.tile_rows);
+    }
+    const int ths[3] = {64, 128, 256};
+    float best = 1e30f;
+    int bk = p->k, bt = p->threads;
+    const double points = (double)p->ny * (double)p->nx;
+    for (int i = 0; i < 8 && kStreamDepths[p->R - 1][p->star][i]; ++i) {
+        const int k = kStreamDepths[p->R - 1][p->star][i];
+        if (p->opt.tb_depth > 0 && k != p->opt.tb_depth) continue;
+        for (int th : ths) {
+            if (p->opt.threads > 0 && th != p->opt.threads) continue;
+            if (configure_stream(p, k, th, p->opt.tile_rows) != STENCIL_OK) continue;
+            // About 2e9 point-steps of work per candidate, at least one launch.
+            const int reps = (int)std::max(1.0, std::min(64.0, 2e9 / (points * k)));
+            float ms = 0.f;
+            stencil_status_t s = time_launch(p, in, reps, st, &ms);
+            if (s != STENCIL_OK) return s;
+            const float per_step = ms / (float)(reps * k);
+            if (per_step < best) {
+                best = per_step;
+                bk = k;
+                bt = th;
+            }
+        }
+    }
+    stencil_status_t s = configure_stream(p, bk, bt, p->opt.tile_rows);
+    if (s != STENCIL_OK) return s;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(bk, bt);
+    return STENCIL_OK;
 }
 
 extern "C" {
@@ -232,6 +344,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     if (ny < 1 || nx < 1) return fail(STENCIL_ERR_INVALID_ARG, "ny and nx must be >= 1");
     if (radius < 1) return fail(STENCIL_ERR_INVALID_ARG, "radius must be >= 1");
     if (radius > kMaxRadius) return fail(STENCIL_ERR_UNSUPPORTED, "radius > 3 is not supported");
+    if (ny > (1LL << 30) || nx > (1LL << 30))
+        return fail(STENCIL_ERR_UNSUPPORTED, "ny and nx must be <= 2^30");
     if (!weights) return fail(STENCIL_ERR_INVALID_ARG, "weights pointer is NULL");
     if (dtype < STENCIL_F32 || dtype > STENCIL_F16) return fail(STENCIL_ERR_INVALID_ARG, "bad dtype");
     if (boundary != STENCIL_BOUNDARY_ZERO && boundary != STENCIL_BOUNDARY_PERIODIC)
@@ -288,8 +402,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
         st = configure_naive(p);
     } else {
         const int k = o.tb_depth > 0 ? o.tb_depth : default_depth(radius, star);
-        const int threads = o.threads > 0 ? o.threads : (k >= 8 ? 128 : 256);
-        st = configure_stream(p, std::min(k, stream_kmax(radius)), threads, o.tile_rows);
+        const int threads = o.threads > 0 ? o.threads : kDefaultThreads;
+        st = configure_stream(p, std::min(k, stream_kmax(radius, star)), threads, o.tile_rows);
     }
     if (st != STENCIL_OK) return bail(st);
 
@@ -357,6 +471,11 @@ stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64
     cudaStream_t st = (cudaStream_t)stream;
     p->last_stream = st;
     const size_t bytes = (size_t)p->ny * p->nx * p->elem;
+    if (p->opt.autotune && !p->tuned && p->kernel == STENCIL_KERNEL_STREAM && T > 0) {
+        stencil_status_t s = autotune(p, in, st);
+        if (s != STENCIL_OK) return s;
+        p->tuned = 1;
+    }
     if (T == 0) {
         if (in != out) CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
         return STENCIL_OK;

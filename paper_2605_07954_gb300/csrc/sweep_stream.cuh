@@ -1,203 +1,371 @@
 // sweep_stream.cuh -- row-streaming, temporally blocked Jacobi sweep (sm_103a).
 //
-// Computes nlev steps of the Jacobi update of Sec. II-C per launch:
+// Computes K steps of the Jacobi update of Sec. II-C per launch:
 //     u^{t+1}[i][j] = sum_{dy,dx} W[dy+R][dx+R] * u~^t[i+dy][j+dx]
 // with u~ zero outside the grid (the fixed zero padding of Sec. IV-A) or
 // wrapped (periodic).
 //
 // Decomposition.  A CTA owns an output tile of `by` rows x `bx` columns.  It
-// loads a strip of bx + 2H columns (H >= R*nlev halo columns per side, the GPU
-// counterpart of the paper's per-tile halo padding, Sec. IV-A step 3, made
-// nlev times deeper so that nlev steps need no exchange with other CTAs) and
-// streams down the rows from y0 - R*nlev to y0 + by - 1 + R*nlev.
+// loads a strip of bx + 2H columns (H >= R*K halo columns per side: the GPU
+// counterpart of the paper's per-tile halo padding, Sec. IV-A step 3, made K
+// times deeper so that K steps need no exchange with other CTAs) and streams
+// down the rows from y0 - R*K to y0 + by - 1 + R*K.
 //
-// Each thread owns 4 adjacent columns.  Time level l+1 is produced from level
-// l as a pipeline along y: when row y of level l arrives, it is the last
-// contribution to output row y-R of level l+1 and the first to row y+R.  A
-// thread therefore keeps 2R+1 partial sums per column and level in registers
-// (a register window sliding down the rows); a completed level-(l+1) row is
-// immediately fed to level l+2 in the same row step.  Only the R columns on
-// each side of a thread's 4 columns cross threads: each level's newest row
-// is written once to a double-buffered shared-memory row and the halo values
-// are read back after one barrier.  The input row comes from HBM with one
-// 16-byte (FP32) or 8-byte (BF16/FP16) vector load per thread; only the level
-// nlev row goes back to HBM.  So HBM traffic is ~(4+4)/nlev bytes per
-// point-step for FP32, plus the halo overlap.
+// Each thread owns 4 adjacent columns, held as two column pairs so that the
+// arithmetic runs as packed FP32x2 FMAs (one instruction, two FMAs).  Time
+// level l+1 is produced from level l as a pipeline along y: when row y of
+// level l arrives it is the last contribution to output row y-R of level l+1
+// and the first to row y+R.  A thread keeps 2R+1 partial sums per column and
+// level in registers (a window sliding down the rows); a completed
+// level-(l+1) row feeds level l+2 in the same row step.  Only the R columns
+// next to a thread's 4 columns cross threads: each level publishes its newest
+// row's edge values to a double-buffered shared-memory array (R = 1: separate
+// left/right edge arrays, so every access is conflict-free and unit stride;
+// R = 2, 3: the whole 16-byte chunk), does the products that need only
+// its own columns, waits at one barrier, then adds the products that need the
+// neighbours' edges.
 //
-// Boundary: with the zero rule, every level's values outside the grid are
-// forced to 0 after they are computed, so the halo stays a frozen zero at
-// every sub-step, exactly as the padding in the paper.  With the periodic
-// rule, loads wrap and nothing is masked.
+// Input rows stream from HBM into a shared-memory ring with cp.async, PF rows
+// ahead (VEC kernels: rows are 16-byte aligned; out-of-grid chunks are
+// zero-filled by the copy).  Kernels for widths that are not a multiple of 4
+// load element by element into registers instead.  Only the level-K row goes
+// back to HBM, so HBM traffic is ~(4+4)/K bytes per point-step for FP32 plus
+// the overlap of neighbouring tiles' halos.
 //
-// Summation order: each output accumulates dy = -R .. R (row by row as rows
-// arrive) and, within a row, dx = -R .. R, with one FMA per weight: the
-// dy-major, dx-minor order of the plain loop.  Star footprints skip the
-// off-axis (zero) weights.
+// Boundary.  With the zero rule, every level's values outside the grid are
+// forced back to 0 after they are computed (only in tiles that touch the
+// boundary), so the halo stays a frozen zero at every sub-step, as the
+// padding does in the paper.  With the periodic rule, loads wrap and nothing
+// is masked.  Rows before a level's first valid row hold finite garbage that
+// never reaches a stored output (a level's valid rows only read valid rows).
+//
+// Summation order: each output accumulates dy = -R .. R as rows arrive; within
+// a row the own-column products come first and the neighbour-column products
+// after the barrier.  Star footprints skip the off-axis (zero) weights.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
 namespace gbst {
 
+constexpr int kStreamMaxThreads = 256;
+constexpr int kStreamPrefetch = 4;  // rows in flight per thread (power of 2)
+
+// Floats of one (level, parity) edge buffer, sized for the largest CTA so
+// that every shared-memory offset is a compile-time constant.
+__host__ __device__ constexpr int stream_buf_floats(int R) {
+    return R == 3 ? 4 * (kStreamMaxThreads + 2) : 2 * R * (kStreamMaxThreads + 2);
+}
+
+// Dynamic shared memory of a launch: the input ring (VEC only) + 2K edge buffers.
+__host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes, bool vec) {
+    return (vec ? kStreamPrefetch * kStreamMaxThreads * 4 * elem_bytes : 0) +
+           2 * K * stream_buf_floats(R) * 4;
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+template <int R>
+__device__ __forceinline__ float2 wgt2(const StreamParams& p, int m, int dx) {
+    return p.w2.w2[m * (2 * R + 1) + dx + R];
+}
+
+// ---- input loading --------------------------------------------------------------
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int n = valid ? BYTES : 0;
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(n));
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gsrc), "r"(n));
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <typename TS>
-__device__ __forceinline__ void load_chunk(const StreamParams& p, long long y, long long c0,
-                                           bool active, float (&v)[4]) {
+__device__ __forceinline__ void smem_chunk_to_f32(const void* src, float (&v)[4]) {
+    if constexpr (sizeof(TS) == 4) {
+        float4 q = *reinterpret_cast<const float4*>(src);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        uint2 raw = *reinterpret_cast<const uint2*>(src);
+        float4 q;
+        if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+            float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&raw.x));
+            float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&raw.y));
+            q = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            float2 a = __half22float2(*reinterpret_cast<__half2*>(&raw.x));
+            float2 b = __half22float2(*reinterpret_cast<__half2*>(&raw.y));
+            q = make_float4(a.x, a.y, b.x, b.y);
+        }
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+}
+
+// Element-wise register load of one chunk (widths that are not a multiple of 4).
+template <typename TS>
+__device__ __forceinline__ void load_chunk_scalar(const StreamParams& p, int y, int c0, bool active,
+                                                  float (&v)[4]) {
     const TS* in = static_cast<const TS*>(p.in);
     v[0] = v[1] = v[2] = v[3] = 0.f;
     if (!active) return;
+    const int nx = (int)p.nx, ny = (int)p.ny;
     if (p.periodic) {
-        const long long yy = wrap_index(y, p.ny);
-        const TS* row = in + yy * p.nx;
-        if (p.vec) {
-            const long long cc = wrap_index(c0, p.nx);
-            float4 q = Storage<TS>::load4(row + cc);
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        } else {
+        const TS* row = in + (size_t)wrap_index(y, ny) * (size_t)nx;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = Storage<TS>::load1(row + wrap_index(c0 + e, p.nx));
-        }
+        for (int e = 0; e < 4; ++e) v[e] = Storage<TS>::load1(row + (int)wrap_index(c0 + e, nx));
         return;
     }
-    if (y < 0 || y >= p.ny) return;
-    const TS* row = in + y * p.nx;
-    if (p.vec && c0 >= 0 && c0 + 4 <= p.nx) {
-        float4 q = Storage<TS>::load4(row + c0);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    } else {
+    if (y < 0 || y >= ny) return;
+    const TS* row = in + (size_t)y * (size_t)nx;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const long long c = c0 + e;
-            if (c >= 0 && c < p.nx) v[e] = Storage<TS>::load1(row + c);
+    for (int e = 0; e < 4; ++e)
+        if (c0 + e >= 0 && c0 + e < nx) v[e] = Storage<TS>::load1(row + c0 + e);
+}
+
+// ---- arithmetic -----------------------------------------------------------------
+
+// Own-column products of one arriving row: pair q holds columns 2q, 2q+1.
+// cur2[0] = (c0,c1), cur2[1] = (c2,c3); mid = (c1,c2).
+template <int R, bool STAR>
+__device__ __forceinline__ void own_products(const StreamParams& p, float2 (&acc)[2 * R + 1][2],
+                                             const float2 (&cur2)[2], float2 mid, int j) {
+    constexpr int D = 2 * R + 1;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        const int slot = (j - m + R + 2 * D) % D;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            bool first = (m == 0);
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                if (STAR && m != R && dx != 0) continue;
+                const int c = 2 * q + dx;  // first source column of the pair
+                if (c < 0 || c + 1 > 3) continue;
+                const float2 src = (c == 0) ? cur2[0] : (c == 2 ? cur2[1] : mid);
+                if (first) {
+                    acc[slot][q] = fmul2(wgt2<R>(p, m, dx), src);
+                    first = false;
+                } else {
+                    acc[slot][q] = ffma2(wgt2<R>(p, m, dx), src, acc[slot][q]);
+                }
+            }
         }
     }
 }
 
-template <int R, bool STAR, int KMAX, typename TS>
-__global__ void __launch_bounds__(256) sweep_stream_kernel(const __grid_constant__ StreamParams p) {
+// Products whose pair touches a neighbour column.  ext[i] = column i - R for
+// i in [0, 4 + 2R): left halo values, own values, right halo values.
+template <int R, bool STAR>
+__device__ __forceinline__ void halo_products(const StreamParams& p, float2 (&acc)[2 * R + 1][2],
+                                              const float (&ext)[4 + 2 * R], int j) {
     constexpr int D = 2 * R + 1;
-    extern __shared__ float4 smem_f4[];
-    float* smem = reinterpret_cast<float*>(smem_f4);
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        if (STAR && m != R) continue;
+        const int slot = (j - m + R + 2 * D) % D;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                const int c = 2 * q + dx;
+                if (c >= 0 && c + 1 <= 3) continue;
+                const float2 src = make_float2(ext[c + R], ext[c + 1 + R]);
+                acc[slot][q] = ffma2(wgt2<R>(p, m, dx), src, acc[slot][q]);
+            }
+        }
+    }
+}
 
-    const int NT = blockDim.x;
-    const int rowlen = 4 * NT + 8;  // 4 padding floats on each side keep 16-byte alignment
-    const int tid = threadIdx.x;
-    const int strip = blockIdx.x % p.strips;
-    const int tile = blockIdx.x / p.strips;
-    const long long x0 = (long long)strip * p.bx;  // first output column of the tile
-    const long long y0 = (long long)tile * p.by;   // first output row of the tile
-    const long long c0 = x0 - p.H + 4LL * tid;     // this thread's first column
-    const int nlev = p.nlev;
-    const long long ybeg = y0 - (long long)R * nlev;
-    const long long ylast = min(y0 + p.by, p.ny);  // one past the last output row
+// One CTA's tile.  EDGE = the tile loads rows or columns outside the grid:
+// loads are bounds-checked (zero rule) or wrapped (periodic), and with the
+// zero rule every level's out-of-grid values are forced to 0.  Interior tiles
+// run without any of that.
+template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE>
+__device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, float* ebuf, int NT,
+                                            int tid, int x0, int y0) {
+    constexpr int D = 2 * R + 1;
+    constexpr int SZ = stream_buf_floats(R);
+    constexpr int PF = kStreamPrefetch;
+    constexpr int CB = 4 * (int)sizeof(TS);  // bytes of one 4-column chunk
+    const int ny = (int)p.ny, nx = (int)p.nx;
+    const int c0 = x0 - p.H + 4 * tid;  // this thread's first column
+    const int ybeg = y0 - R * K;
+    const int ylast = min(y0 + p.by, ny);  // one past the last output row
     const bool active = 4 * tid < p.bx + 2 * p.H;
+    const bool periodic = EDGE && p.periodic != 0;
+    const bool mask = EDGE && !periodic;
 
-    for (int i = tid; i < 2 * KMAX * rowlen; i += NT) smem[i] = 0.f;
-
-    // Columns outside the grid (zero rule) are forced to zero at every level.
     bool col_in[4];
     bool any_out = false;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        col_in[e] = p.periodic || (c0 + e >= 0 && c0 + e < p.nx);
+        col_in[e] = !mask || (c0 + e >= 0 && c0 + e < nx);
         any_out |= !col_in[e];
     }
-    const bool store_chunk = active && c0 >= x0 && c0 + 4 <= x0 + p.bx && c0 < p.nx;
+    const bool store_chunk = active && c0 >= x0 && c0 + 4 <= x0 + p.bx && c0 < nx;
 
-    float acc[KMAX][D][4];
+    float2 acc[K][D][2];
 #pragma unroll
-    for (int l = 0; l < KMAX; ++l)
+    for (int l = 0; l < K; ++l)
 #pragma unroll
-        for (int m = 0; m < D; ++m)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[l][m][e] = 0.f;
+        for (int m = 0; m < D; ++m) acc[l][m][0] = acc[l][m][1] = make_float2(0.f, 0.f);
 
-    const int nreal = (int)(ylast - y0) + 2 * R * nlev;  // row steps that matter
-    const int nsteps = (nreal + D - 1) / D * D;          // rounded up to the unroll
+    const int nreal = (ylast - y0) + 2 * R * K;  // row steps that matter
+    const int nsteps = (nreal + D - 1) / D * D;  // rounded up to the unroll
 
-    float nxt[4];
-    load_chunk<TS>(p, ybeg, c0, active, nxt);
-    __syncthreads();
+    // VEC: the chunk this thread copies for row y.
+    const TS* gin = static_cast<const TS*>(p.in);
+    const int cw = periodic ? (int)wrap_index(c0, nx) : c0;
+    const bool col_ok = !EDGE || (active && (periodic || (c0 >= 0 && c0 + 4 <= nx)));
+    char* my_ring = ring + tid * CB;
+    const TS* my_src = gin + (EDGE ? 0 : (ptrdiff_t)ybeg * nx + c0);
+    auto issue_row = [&](int s) {
+        bool ok = s < nsteps;
+        const TS* src;
+        if constexpr (EDGE) {
+            const int y = ybeg + s;
+            int yy = y;
+            ok = ok && col_ok;
+            if (periodic) {
+                yy = (int)wrap_index(y, ny);
+            } else {
+                ok = ok && y >= 0 && y < ny;
+            }
+            src = ok ? gin + (size_t)yy * (size_t)nx + cw : gin;
+        } else {
+            src = ok ? my_src + (size_t)s * (size_t)nx : gin;
+        }
+        cp_async<CB>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), src, ok);
+        cp_async_commit();
+    };
+
+    float nreg0[4], nreg1[4];  // register prefetch (non-VEC)
+    if constexpr (VEC) {
+#pragma unroll
+        for (int s = 0; s < PF - 1; ++s) issue_row(s);
+    } else {
+        load_chunk_scalar<TS>(p, ybeg, c0, active, nreg0);
+        load_chunk_scalar<TS>(p, ybeg + 1, c0, active, nreg1);
+    }
 
     for (int s0 = 0; s0 < nsteps; s0 += D) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const int s = s0 + j;
-            float cur[4] = {nxt[0], nxt[1], nxt[2], nxt[3]};
-            if (s + 1 < nsteps) load_chunk<TS>(p, ybeg + s + 1, c0, active, nxt);
-            const int par = s & 1;
+            float cur[4];
+            if constexpr (VEC) {
+                issue_row(s + PF - 1);
+                cp_async_wait<PF - 1>();
+                smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), cur);
+            } else {
 #pragma unroll
-            for (int l = 0; l < KMAX; ++l) {
+                for (int e = 0; e < 4; ++e) { cur[e] = nreg0[e]; nreg0[e] = nreg1[e]; }
+                if (s + 2 < nsteps) load_chunk_scalar<TS>(p, ybeg + s + 2, c0, active, nreg1);
+            }
+            float* bpar = ebuf + (s & 1) * SZ;
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
                 // Level l's row ybeg - l*R + s arrives; it feeds level l+1.
-                if (l < nlev && s >= 2 * l * R) {
-                    float* row = smem + (2 * l + par) * rowlen + 4;
-                    *reinterpret_cast<float4*>(row + 4 * tid) =
-                        make_float4(cur[0], cur[1], cur[2], cur[3]);
-                    __syncthreads();
-                    float h[4 + 2 * R];
+                float* B = bpar + 2 * l * SZ;
+                if constexpr (R == 1) {
+                    B[tid + 1] = cur[0];
+                    B[kStreamMaxThreads + 2 + tid + 1] = cur[3];
+                } else {
+                    reinterpret_cast<float4*>(B)[tid + 1] = make_float4(cur[0], cur[1], cur[2], cur[3]);
+                }
+                const float2 cur2[2] = {make_float2(cur[0], cur[1]), make_float2(cur[2], cur[3])};
+                own_products<R, STAR>(p, acc[l], cur2, make_float2(cur[1], cur[2]), j);
+                __syncthreads();
+                float ext[4 + 2 * R];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) h[R + e] = cur[e];
-                    if constexpr (R == 1) {
-                        h[0] = row[4 * tid - 1];
-                        h[5] = row[4 * tid + 4];
-                    } else if constexpr (R == 2) {
-                        float2 a = *reinterpret_cast<const float2*>(row + 4 * tid - 2);
-                        float2 b = *reinterpret_cast<const float2*>(row + 4 * tid + 4);
-                        h[0] = a.x; h[1] = a.y; h[2 * R + 4 - 2] = b.x; h[2 * R + 4 - 1] = b.y;
-                    } else {
-                        float4 a = *reinterpret_cast<const float4*>(row + 4 * tid - 4);
-                        float4 b = *reinterpret_cast<const float4*>(row + 4 * tid + 4);
-                        h[0] = a.y; h[1] = a.z; h[2] = a.w;
-                        h[R + 4 + 0] = b.x; h[R + 4 + 1] = b.y; h[R + 4 + 2] = b.z;
+                for (int e = 0; e < 4; ++e) ext[R + e] = cur[e];
+                if constexpr (R == 1) {
+                    ext[0] = B[kStreamMaxThreads + 2 + tid];
+                    ext[5] = B[tid + 2];
+                } else {
+                    float4 a = reinterpret_cast<const float4*>(B)[tid];
+                    float4 b = reinterpret_cast<const float4*>(B)[tid + 2];
+                    const float lft[4] = {a.x, a.y, a.z, a.w}, rgt[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        ext[i] = lft[4 - R + i];
+                        ext[R + 4 + i] = rgt[i];
                     }
-                    // m = dy + R: this row is the (m+1)-th contribution to output row
-                    // (arriving row) - dy, held in slot (j - m + R) mod D.
+                }
+                halo_products<R, STAR>(p, acc[l], ext, j);
+                // Output row (arriving row) - R of level l+1 is complete.
+                const int cs = (j + R + 1) % D;
+                cur[0] = acc[l][cs][0].x; cur[1] = acc[l][cs][0].y;
+                cur[2] = acc[l][cs][1].x; cur[3] = acc[l][cs][1].y;
+                if constexpr (EDGE) {
+                    if (mask) {
+                        const int yo = ybeg - (l + 1) * R + s;
+                        if (yo < 0 || yo >= ny) {
 #pragma unroll
-                    for (int m = 0; m < D; ++m) {
-                        const int slot = (j - m + R + 2 * D) % D;
-                        if (STAR && m != R) {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float wv = p.w.w[m * D + R];
-                                acc[l][slot][e] = (m == 0) ? wv * h[R + e]
-                                                           : fmaf(wv, h[R + e], acc[l][slot][e]);
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                float a = (m == 0) ? p.w.w[m * D] * h[e]
-                                                   : fmaf(p.w.w[m * D], h[e], acc[l][slot][e]);
-#pragma unroll
-                                for (int dx = 1; dx < D; ++dx) a = fmaf(p.w.w[m * D + dx], h[e + dx], a);
-                                acc[l][slot][e] = a;
-                            }
+                            for (int e = 0; e < 4; ++e) cur[e] = 0.f;
                         }
-                    }
-                    // Output row (arriving row) - R of level l+1 is complete.
-                    const int cs = (j + R + 1) % D;
-                    const long long yo = ybeg - (long long)(l + 1) * R + s;
-                    const bool row_out = !p.periodic && (yo < 0 || yo >= p.ny);
+                        if (any_out) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        float v = acc[l][cs][e];
-                        if (row_out || (any_out && !col_in[e])) v = 0.f;
-                        cur[e] = v;
+                            for (int e = 0; e < 4; ++e) cur[e] = col_in[e] ? cur[e] : 0.f;
+                        }
                     }
                 }
             }
-            // cur holds level nlev's row ybeg - nlev*R + s.
-            const long long yo = ybeg - (long long)R * nlev + s;
+            // cur holds level K's row ybeg - K*R + s.
+            const int yo = ybeg - R * K + s;
             if (store_chunk && yo >= y0 && yo < ylast) {
-                TS* orow = static_cast<TS*>(p.out) + yo * p.nx;
-                if (p.vec && c0 + 4 <= p.nx) {
+                TS* orow = static_cast<TS*>(p.out) + (size_t)yo * (size_t)nx;
+                if (VEC) {
                     Storage<TS>::store4(orow + c0, make_float4(cur[0], cur[1], cur[2], cur[3]));
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        if (c0 + e < p.nx) Storage<TS>::store1(orow + c0 + e, cur[e]);
+                        if (c0 + e < nx) Storage<TS>::store1(orow + c0 + e, cur[e]);
                 }
             }
         }
     }
+    if constexpr (VEC) cp_async_wait<0>();
+}
+
+template <int R, bool STAR, int K, typename TS, bool VEC>
+__global__ void __launch_bounds__(kStreamMaxThreads)
+    sweep_stream_kernel(const __grid_constant__ StreamParams p) {
+    constexpr int D = 2 * R + 1;
+    constexpr int PF = kStreamPrefetch;
+    constexpr int CB = 4 * (int)sizeof(TS);
+    extern __shared__ float4 smem_f4[];
+    char* ring = reinterpret_cast<char*>(smem_f4);
+    float* ebuf = reinterpret_cast<float*>(ring + (VEC ? PF * kStreamMaxThreads * CB : 0));
+    const int NT = blockDim.x;
+    const int tid = threadIdx.x;
+    const int strip = blockIdx.x % p.strips;
+    const int tile = blockIdx.x / p.strips;
+    const int x0 = strip * p.bx;  // first output column of the tile
+    const int y0 = tile * p.by;   // first output row of the tile
+
+    for (int i = tid; i < 2 * K * stream_buf_floats(R); i += NT) ebuf[i] = 0.f;
+    __syncthreads();
+
+    // Interior: every row this CTA loads (including the rounded-up tail of the
+    // row loop) and every column of its strip lies inside the grid.
+    const int ny = (int)p.ny, nx = (int)p.nx;
+    const int ylast = min(y0 + p.by, ny);
+    const bool interior = VEC && y0 - R * K >= 0 && ylast + R * K + D <= ny && x0 - p.H >= 0 &&
+                          x0 - p.H + 4 * NT <= nx;
+    if (interior)
+        stream_tile<R, STAR, K, TS, VEC, false>(p, ring, ebuf, NT, tid, x0, y0);
+    else
+        stream_tile<R, STAR, K, TS, VEC, true>(p, ring, ebuf, NT, tid, x0, y0);
 }
 
 // Host-side handle of one instantiation.

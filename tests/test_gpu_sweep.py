@@ -62,18 +62,23 @@ def test_parity_small_auto(oracle, name, boundary, shape):
     assert rel_linf(got, ref) <= fp32_elem_tol(T, _taps(W)), info
 
 
+# Depths the streaming kernel is instantiated for, per (radius, shape).
+DEPTHS = {(1, "box"): [1, 2, 3, 4, 6, 8], (1, "star"): [1, 2, 3, 4, 6, 8],
+          (3, "box"): [1, 2], (3, "star"): [1, 2, 3, 4]}
+
+
 @pytest.mark.parametrize("name", PATTERNS)
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8])
 @pytest.mark.parametrize("threads,tile_rows", [(32, 7), (64, 33)])
 def test_parity_depths_small_tiles(oracle, name, k, threads, tile_rows):
-    """Forced small CTAs and odd tile heights: many tiles, ragged last strip/tile."""
+    """Forced small CTAs and odd tile heights: many tiles, ragged last strip/tile.
+    T = 2k + 5 also exercises the remainder launches (greedy split of T mod k)."""
     shape, r = inputs.PATTERNS[name]
-    kmax = {1: 8, 2: 4, 3: 4}[r]
-    if k > kmax or 4 * threads - 2 * ((r * k + 3) // 4 * 4) < 4:
+    if k not in DEPTHS[(r, shape)] or 4 * threads - 2 * ((r * k + 3) // 4 * 4) < 4:
         pytest.skip("configuration outside the instantiated range")
     W = inputs.pattern_weights(name)
     u0 = inputs.field(45, 150 if threads == 32 else 601)
-    T = 2 * k + 1
+    T = 2 * k + 5
     ref = oracle.sweep_f64(u0, W, T)
     got, info = _gpu_run(u0, W, T, tb_depth=k, threads=threads, tile_rows=tile_rows)
     assert info["tb_depth"] == k and info["ctas"] > 4
@@ -286,3 +291,23 @@ def test_moderate_T1000_full_oracle(oracle):
         e2, ei = rel_l2(got, ref), rel_linf(got, ref)
         print(f"{name} T={T} relL2={e2:.3e} relLinf={ei:.3e}")
         assert e2 <= fp32_tol(T) and ei <= fp32_elem_tol(T, _taps(W))
+
+
+@pytest.mark.parametrize("name", ["box9", "star13"])
+def test_autotune_first_run(oracle, name):
+    """opt.autotune times the candidate depths/CTA sizes on the first run and
+    keeps one of them; the result still matches the oracle."""
+    W = inputs.pattern_weights(name)
+    u0 = inputs.field(300, 520)
+    ref = oracle.sweep_f64(u0, W, 40)
+    p = _plan(300, 520, W, autotune=True)
+    x = torch.from_numpy(u0).cuda()
+    y = p.run(x, 40)
+    torch.cuda.synchronize()
+    info = p.info()
+    shape, r = inputs.PATTERNS[name]
+    assert info["tb_depth"] in DEPTHS[(r, shape)]
+    assert info["threads"] % 32 == 0 and 32 <= info["threads"] <= 256
+    assert rel_l2(y.cpu().numpy(), ref) <= fp32_tol(40)
+    assert torch.equal(x, torch.from_numpy(u0).cuda())
+    p.close()
