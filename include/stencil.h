@@ -152,6 +152,38 @@ int64_t stencil_run_launches(const stencil_plan_t* plan, int64_t T);
  */
 stencil_status_t stencil_plan_status(stencil_plan_t* plan);
 
+/*
+ * ---- Allocation-free sweep (no counterpart in the paper) ----------------------
+ *
+ * For callers that must not allocate device memory when they run a sweep: an
+ * inference-engine plugin whose enqueue step may not allocate, code running
+ * while a framework's caching allocator already holds the free memory, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation.  It needs no plan (stencil_plan_create allocates a
+ * workspace) and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Same operation and argument meaning as stencil_plan_create + stencil_run,
+ * with the library's default configuration (no autotuning).  The ping-pong
+ * buffer is a fixed device array of STENCIL_NOALLOC_MAX_BYTES inside the
+ * library, reserved on every GPU that loads the library until the process
+ * exits.  Grids with ny*nx*element_size above that limit are rejected with
+ * STENCIL_ERR_UNSUPPORTED (see stencil_noalloc_last_error()).
+ *   - The first call on each device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; nothing
+ *     in it needs to start at zero.  Calls whose work overlaps on the GPU (two
+ *     streams at once, or two threads) race on the array and give wrong results.
+ *   - in == out is allowed; T == 0 copies in to out.
+ */
+#define STENCIL_NOALLOC_MAX_BYTES (64ull << 20)
+
+stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const float* weights,
+                                     int dtype, int boundary, const void* in, void* out, int64_t T,
+                                     stencil_stream_t stream);
+
+/* Message for the last failure of stencil_run_noalloc on the calling thread. */
+const char* stencil_noalloc_last_error(void);
+
 /* Human-readable name of a status code (static string). */
 const char* stencil_status_string(stencil_status_t status);
 

@@ -56,6 +56,9 @@ _PROTOS = {
     "stencil_status_string": (ctypes.c_char_p, [_i32]),
     "stencil_last_error": (ctypes.c_char_p, []),
     "stencil_version": (_i32, []),
+    "stencil_run_noalloc": (_i32, [_i64, _i64, _i32, ctypes.POINTER(ctypes.c_float), _i32, _i32,
+                                   _vp, _vp, _i64, _vp]),
+    "stencil_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
