@@ -153,6 +153,72 @@ int64_t stencil_run_launches(const stencil_plan_t* plan, int64_t T);
 stencil_status_t stencil_plan_status(stencil_plan_t* plan);
 
 /*
+ * ---- Batches: many independent grids in one persistent launch ----------------
+ *
+ * Each grid of a batch is its own Jacobi problem (Sec. II-C): its own size,
+ * radius, weights, boundary and number of steps T.  stencil_run_batched runs
+ * them all in one persistent kernel per radius (plus one launch per leftover
+ * depth when k does not divide some T), replayed from a CUDA graph that the
+ * first call captures.  The result of every grid is bit-identical to
+ * stencil_run on a plan of the same grid (same arithmetic per point).
+ */
+typedef struct {
+    int64_t ny, nx;         /* grid rows and columns, each >= 1                        */
+    int radius;             /* 1..3                                                   */
+    const float* weights;   /* HOST, (2r+1)^2 FP32, as for stencil_plan_create; copied */
+    int boundary;           /* stencil_boundary_t (periodic needs nx % 4 == 0)        */
+    int64_t T;              /* steps for this grid, >= 0                              */
+    const void* in;         /* DEVICE, ny*nx dense row-major; only read               */
+    void* out;              /* DEVICE, ny*nx dense row-major; may equal in            */
+} stencil_grid_desc_t;
+
+typedef struct {
+    int tb_depth;           /* steps per work item k; 0 = 4, capped per radius (8 / 2 / 2) */
+    int threads;            /* CTA size, multiple of 32 in 32..256; 0 = 128            */
+    int tile_rows;          /* rows per tile; 0 = 256 (at least R*k + 2R + 2)          */
+    int autotune;           /* 1: time each depth and CTA size on the whole batch at create */
+    int timeout_ms;         /* bound of every device-side wait; 0 = 2000 ms             */
+    int debug_withhold_item;/* test hook: 1 + index of a work item whose completion is never
+                               published, so dependent waits run out (0 = off)          */
+} stencil_batch_options_t;
+
+typedef struct {
+    int n;                  /* grids                                                   */
+    int tb_depth, threads;
+    int tiles;              /* tiles over all grids                                     */
+    int64_t items;          /* work items (tile x time block) per run                  */
+    int launches;           /* kernel launches per run                                 */
+    int ctas;               /* CTAs of the first (persistent) launch                   */
+    int64_t point_steps;    /* sum over grids of ny*nx*T                                */
+} stencil_batch_info_t;
+
+typedef struct stencil_batch stencil_batch_t;
+
+/*
+ * Create a batch of n grids.  Copies the descriptors and weights; the device
+ * pointers must stay valid while the batch is used.  Allocates two padded
+ * work grids per grid (row pitch rounded up to 4 elements), the item queue
+ * and the counters.  With opt->autotune the batch is run several times here.
+ */
+stencil_status_t stencil_batch_create(stencil_batch_t** batch, int n, const stencil_grid_desc_t* grids,
+                                      int dtype, const stencil_batch_options_t* opt);
+
+/* Run every grid of the batch on `stream` (graph captured on the first call;
+ * that first call must not be inside a stream capture of the caller). */
+stencil_status_t stencil_run_batched(stencil_batch_t* batch, stencil_stream_t stream);
+
+/* Synchronise the device and read the batch's status word (STENCIL_ERR_TIMEOUT
+ * if a dependency wait ran out).  Clears the word. */
+stencil_status_t stencil_batch_status(stencil_batch_t* batch);
+
+stencil_status_t stencil_batch_info(const stencil_batch_t* batch, stencil_batch_info_t* info);
+
+void stencil_batch_destroy(stencil_batch_t* batch);
+
+/* Message for the last failure of a stencil_batch_* call on the calling thread. */
+const char* stencil_batch_last_error(void);
+
+/*
  * ---- Allocation-free sweep (no counterpart in the paper) ----------------------
  *
  * For callers that must not allocate device memory when they run a sweep: an

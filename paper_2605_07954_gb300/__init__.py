@@ -111,6 +111,65 @@ class Plan:
         check(_capi.load().stencil_plan_status(self._h), "stencil_plan_status")
 
 
+class Batch:
+    """Many independent grids run by one persistent launch (CUDA-graph replayed).
+
+    ``grids`` is a list of dicts with keys ``x`` (input, CUDA tensor), ``out``
+    (output tensor, may be ``x``), ``weights`` ((2r+1)^2 array), ``T`` and
+    optionally ``boundary``.  The tensors must stay alive while the batch is used.
+    """
+
+    def __init__(self, grids, dtype: str = "f32", tb_depth: int = 0, threads: int = 0,
+                 tile_rows: int = 0, autotune: bool = False, timeout_ms: int = 0,
+                 debug_withhold_item: int = 0):
+        lib = _capi.load()
+        n = len(grids)
+        descs = (_capi.stencil_grid_desc_t * n)()
+        self._keep = []
+        for i, g in enumerate(grids):
+            w = np.ascontiguousarray(np.asarray(g["weights"], dtype=np.float32))
+            self._keep.append(w)
+            x, out = g["x"], g["out"]
+            if _torch_dtype_name(x.dtype) != dtype or out.dtype != x.dtype:
+                raise ValueError("grid tensors must match the batch dtype")
+            if not (x.is_cuda and x.is_contiguous() and out.is_contiguous() and x.shape == out.shape):
+                raise ValueError("grids must be contiguous CUDA tensors of equal shape")
+            descs[i] = _capi.stencil_grid_desc_t(
+                x.shape[0], x.shape[1], w.shape[0] // 2,
+                w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                BOUNDARIES[g.get("boundary", "zero")], int(g["T"]), x.data_ptr(), out.data_ptr())
+        opt = _capi.stencil_batch_options_t(int(tb_depth), int(threads), int(tile_rows),
+                                            int(bool(autotune)), int(timeout_ms),
+                                            int(debug_withhold_item))
+        h = ctypes.c_void_p()
+        check(lib.stencil_batch_create(ctypes.byref(h), n, descs, DTYPES[dtype], ctypes.byref(opt)),
+              "stencil_batch_create")
+        self._h = h
+
+    def run(self):
+        check(_capi.load().stencil_run_batched(self._h, _current_stream_handle()),
+              "stencil_run_batched")
+
+    def status(self):
+        check(_capi.load().stencil_batch_status(self._h), "stencil_batch_status")
+
+    def info(self) -> dict:
+        i = _capi.stencil_batch_info_t()
+        check(_capi.load().stencil_batch_info(self._h, ctypes.byref(i)), "stencil_batch_info")
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _capi.load().stencil_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def run(x, weights, T: int, boundary: str = "zero", **options):
     """One-shot convenience: plan, run on the current stream, return u_T."""
     p = Plan(x.shape[0], x.shape[1], weights, dtype=_torch_dtype_name(x.dtype),
@@ -122,4 +181,4 @@ def run(x, weights, T: int, boundary: str = "zero", **options):
     return y
 
 
-__all__ = ["Plan", "run", "StencilError", "DTYPES", "BOUNDARIES"]
+__all__ = ["Plan", "Batch", "run", "StencilError", "DTYPES", "BOUNDARIES"]

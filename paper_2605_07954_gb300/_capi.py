@@ -40,6 +40,24 @@ class stencil_plan_info_t(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64)]
 
 
+class stencil_grid_desc_t(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int64), ("nx", ctypes.c_int64), ("radius", ctypes.c_int),
+                ("weights", ctypes.POINTER(ctypes.c_float)), ("boundary", ctypes.c_int),
+                ("T", ctypes.c_int64), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class stencil_batch_options_t(ctypes.Structure):
+    _fields_ = [("tb_depth", ctypes.c_int), ("threads", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("timeout_ms", ctypes.c_int),
+                ("debug_withhold_item", ctypes.c_int)]
+
+
+class stencil_batch_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("tb_depth", ctypes.c_int), ("threads", ctypes.c_int),
+                ("tiles", ctypes.c_int), ("items", ctypes.c_int64), ("launches", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("point_steps", ctypes.c_int64)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int
@@ -56,6 +74,13 @@ _PROTOS = {
     "stencil_status_string": (ctypes.c_char_p, [_i32]),
     "stencil_last_error": (ctypes.c_char_p, []),
     "stencil_version": (_i32, []),
+    "stencil_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(stencil_grid_desc_t),
+                                    _i32, ctypes.POINTER(stencil_batch_options_t)]),
+    "stencil_run_batched": (_i32, [_vp, _vp]),
+    "stencil_batch_status": (_i32, [_vp]),
+    "stencil_batch_info": (_i32, [_vp, ctypes.POINTER(stencil_batch_info_t)]),
+    "stencil_batch_destroy": (None, [_vp]),
+    "stencil_batch_last_error": (ctypes.c_char_p, []),
     "stencil_run_noalloc": (_i32, [_i64, _i64, _i32, ctypes.POINTER(ctypes.c_float), _i32, _i32,
                                    _vp, _vp, _i64, _vp]),
     "stencil_noalloc_last_error": (ctypes.c_char_p, []),
@@ -95,7 +120,12 @@ class StencilError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib = load()
         name = lib.stencil_status_string(status).decode()
-        msg = lib.stencil_last_error().decode()
+        if "batch" in where:
+            msg = lib.stencil_batch_last_error().decode()
+        elif "noalloc" in where:
+            msg = lib.stencil_noalloc_last_error().decode()
+        else:
+            msg = lib.stencil_last_error().decode()
         super().__init__(f"{where}: {name}: {msg}")
         self.status = status
 

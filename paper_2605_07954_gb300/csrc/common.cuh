@@ -31,6 +31,7 @@ struct StreamParams {
     const void* in;
     void* out;
     long long ny, nx;
+    long long ld;   // row pitch of in and out, in elements (>= nx; a multiple of 4 when vec)
     int nlev;      // time levels (Jacobi steps) this launch advances, 1..KMAX
     int H;         // halo columns loaded on each side of a strip (multiple of 4, >= R*nlev)
     int bx;        // output columns per strip (multiple of 4)

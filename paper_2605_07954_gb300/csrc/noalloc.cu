@@ -148,6 +148,7 @@ stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const f
     StreamParams base{};
     base.ny = ny;
     base.nx = nx;
+    base.ld = nx;
     base.periodic = boundary == STENCIL_BOUNDARY_PERIODIC;
     int star = 1;
     for (int a = 0; a < D; ++a)

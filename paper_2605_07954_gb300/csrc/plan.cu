@@ -210,6 +210,7 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
     sp.out = dst;
     sp.ny = p->ny;
     sp.nx = p->nx;
+    sp.ld = p->nx;
     sp.nlev = nlev;
     sp.H = p->H;
     sp.bx = p->bx;

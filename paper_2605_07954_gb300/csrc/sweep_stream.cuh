@@ -68,9 +68,23 @@ __host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-template <int R>
-__device__ __forceinline__ float2 wgt2(const StreamParams& p, int m, int dx) {
-    return p.w2.w2[m * (2 * R + 1) + dx + R];
+// Weight sources for the tile body.  ParamWeights reads the (w, w) pairs from
+// the kernel parameters (the constant bank); RegWeights holds a grid's pairs
+// in registers (batched kernel, one weight set per grid).
+struct ParamWeights {
+    const StreamParams& p;
+    __device__ __forceinline__ float2 w2(int i) const { return p.w2.w2[i]; }
+};
+
+template <int N>
+struct RegWeights {
+    float2 w[N];
+    __device__ __forceinline__ float2 w2(int i) const { return w[i]; }
+};
+
+template <int R, class WS>
+__device__ __forceinline__ float2 wgt2(const WS& ws, int m, int dx) {
+    return ws.w2(m * (2 * R + 1) + dx + R);
 }
 
 // ---- input loading --------------------------------------------------------------
@@ -119,13 +133,13 @@ __device__ __forceinline__ void load_chunk_scalar(const StreamParams& p, int y, 
     if (!active) return;
     const int nx = (int)p.nx, ny = (int)p.ny;
     if (p.periodic) {
-        const TS* row = in + (size_t)wrap_index(y, ny) * (size_t)nx;
+        const TS* row = in + (size_t)wrap_index(y, ny) * (size_t)p.ld;
 #pragma unroll
         for (int e = 0; e < 4; ++e) v[e] = Storage<TS>::load1(row + (int)wrap_index(c0 + e, nx));
         return;
     }
     if (y < 0 || y >= ny) return;
-    const TS* row = in + (size_t)y * (size_t)nx;
+    const TS* row = in + (size_t)y * (size_t)p.ld;
 #pragma unroll
     for (int e = 0; e < 4; ++e)
         if (c0 + e >= 0 && c0 + e < nx) v[e] = Storage<TS>::load1(row + c0 + e);
@@ -135,8 +149,8 @@ __device__ __forceinline__ void load_chunk_scalar(const StreamParams& p, int y, 
 
 // Own-column products of one arriving row: pair q holds columns 2q, 2q+1.
 // cur2[0] = (c0,c1), cur2[1] = (c2,c3); mid = (c1,c2).
-template <int R, bool STAR>
-__device__ __forceinline__ void own_products(const StreamParams& p, float2 (&acc)[2 * R + 1][2],
+template <int R, bool STAR, class WS>
+__device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 1][2],
                                              const float2 (&cur2)[2], float2 mid, int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
@@ -164,8 +178,8 @@ __device__ __forceinline__ void own_products(const StreamParams& p, float2 (&acc
 
 // Products whose pair touches a neighbour column.  ext[i] = column i - R for
 // i in [0, 4 + 2R): left halo values, own values, right halo values.
-template <int R, bool STAR>
-__device__ __forceinline__ void halo_products(const StreamParams& p, float2 (&acc)[2 * R + 1][2],
+template <int R, bool STAR, class WS>
+__device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R + 1][2],
                                               const float (&ext)[4 + 2 * R], int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
@@ -189,14 +203,15 @@ __device__ __forceinline__ void halo_products(const StreamParams& p, float2 (&ac
 // loads are bounds-checked (zero rule) or wrapped (periodic), and with the
 // zero rule every level's out-of-grid values are forced to 0.  Interior tiles
 // run without any of that.
-template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE>
-__device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, float* ebuf, int NT,
-                                            int tid, int x0, int y0) {
+template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, class WS>
+__device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws, char* ring,
+                                            float* ebuf, int NT, int tid, int x0, int y0) {
     constexpr int D = 2 * R + 1;
     constexpr int SZ = stream_buf_floats(R);
     constexpr int PF = kStreamPrefetch;
     constexpr int CB = 4 * (int)sizeof(TS);  // bytes of one 4-column chunk
     const int ny = (int)p.ny, nx = (int)p.nx;
+    const size_t ld = (size_t)p.ld;
     const int c0 = x0 - p.H + 4 * tid;  // this thread's first column
     const int ybeg = y0 - R * K;
     const int ylast = min(y0 + p.by, ny);  // one past the last output row
@@ -225,9 +240,11 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, f
     // VEC: the chunk this thread copies for row y.
     const TS* gin = static_cast<const TS*>(p.in);
     const int cw = periodic ? (int)wrap_index(c0, nx) : c0;
-    const bool col_ok = !EDGE || (active && (periodic || (c0 >= 0 && c0 + 4 <= nx)));
+    // A whole chunk is copied when it lies inside the row pitch; with the zero
+    // rule, columns in [nx, ld) are masked like any other out-of-grid column.
+    const bool col_ok = !EDGE || (active && (periodic || (c0 >= 0 && c0 + 4 <= (int)ld)));
     char* my_ring = ring + tid * CB;
-    const TS* my_src = gin + (EDGE ? 0 : (ptrdiff_t)ybeg * nx + c0);
+    const TS* my_src = gin + (EDGE ? 0 : (ptrdiff_t)ybeg * (ptrdiff_t)ld + c0);
     auto issue_row = [&](int s) {
         bool ok = s < nsteps;
         const TS* src;
@@ -240,9 +257,9 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, f
             } else {
                 ok = ok && y >= 0 && y < ny;
             }
-            src = ok ? gin + (size_t)yy * (size_t)nx + cw : gin;
+            src = ok ? gin + (size_t)yy * ld + cw : gin;
         } else {
-            src = ok ? my_src + (size_t)s * (size_t)nx : gin;
+            src = ok ? my_src + (size_t)s * ld : gin;
         }
         cp_async<CB>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), src, ok);
         cp_async_commit();
@@ -283,7 +300,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, f
                     reinterpret_cast<float4*>(B)[tid + 1] = make_float4(cur[0], cur[1], cur[2], cur[3]);
                 }
                 const float2 cur2[2] = {make_float2(cur[0], cur[1]), make_float2(cur[2], cur[3])};
-                own_products<R, STAR>(p, acc[l], cur2, make_float2(cur[1], cur[2]), j);
+                own_products<R, STAR>(ws, acc[l], cur2, make_float2(cur[1], cur[2]), j);
                 __syncthreads();
                 float ext[4 + 2 * R];
 #pragma unroll
@@ -301,7 +318,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, f
                         ext[R + 4 + i] = rgt[i];
                     }
                 }
-                halo_products<R, STAR>(p, acc[l], ext, j);
+                halo_products<R, STAR>(ws, acc[l], ext, j);
                 // Output row (arriving row) - R of level l+1 is complete.
                 const int cs = (j + R + 1) % D;
                 cur[0] = acc[l][cs][0].x; cur[1] = acc[l][cs][0].y;
@@ -323,7 +340,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, char* ring, f
             // cur holds level K's row ybeg - K*R + s.
             const int yo = ybeg - R * K + s;
             if (store_chunk && yo >= y0 && yo < ylast) {
-                TS* orow = static_cast<TS*>(p.out) + (size_t)yo * (size_t)nx;
+                TS* orow = static_cast<TS*>(p.out) + (size_t)yo * ld;
                 if (VEC) {
                     Storage<TS>::store4(orow + c0, make_float4(cur[0], cur[1], cur[2], cur[3]));
                 } else {
@@ -362,10 +379,11 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
     const int ylast = min(y0 + p.by, ny);
     const bool interior = VEC && y0 - R * K >= 0 && ylast + R * K + D <= ny && x0 - p.H >= 0 &&
                           x0 - p.H + 4 * NT <= nx;
+    const ParamWeights ws{p};
     if (interior)
-        stream_tile<R, STAR, K, TS, VEC, false>(p, ring, ebuf, NT, tid, x0, y0);
+        stream_tile<R, STAR, K, TS, VEC, false>(p, ws, ring, ebuf, NT, tid, x0, y0);
     else
-        stream_tile<R, STAR, K, TS, VEC, true>(p, ring, ebuf, NT, tid, x0, y0);
+        stream_tile<R, STAR, K, TS, VEC, true>(p, ws, ring, ebuf, NT, tid, x0, y0);
 }
 
 // Host-side handle of one instantiation.

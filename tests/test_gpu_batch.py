@@ -1,0 +1,146 @@
+"""GPU tests of the batched path: many grids in one persistent, graph-replayed launch.
+
+Every grid of a batch must give exactly the bits of a single-grid stencil_run
+(the arithmetic per point does not depend on tiling or depth), and match the
+FP64 oracle within the FP32 gate.  The 256-grid workload (sides log-uniform
+in [64, 2048], half Heat-5pt and half Box-9pt with random normalised weights,
+200 steps) runs in full.
+"""
+import numpy as np
+import pytest
+
+from paper_2605_07954_gb300 import inputs
+from _util import fp32_tol, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_07954_gb300 import build
+    build.build()
+
+
+def _single(x, W, T, boundary):
+    from paper_2605_07954_gb300 import Plan
+    p = Plan(x.shape[0], x.shape[1], W, boundary=boundary)
+    y = p.run(x, T)
+    torch.cuda.synchronize()
+    p.close()
+    return y
+
+
+def _mixed_grids():
+    """Ragged widths, odd heights, tiny and multi-tile grids, T not a multiple of k."""
+    rng = np.random.default_rng(31)
+    shapes = [(64, 64), (67, 203), (300, 517), (129, 1000), (5, 7), (1, 33), (600, 600),
+              (40, 2100), (257, 96), (33, 1), (800, 130), (2, 2)]
+    grids = []
+    for i, (ny, nx) in enumerate(shapes):
+        kind = ["heat5r", "box9", "star13", "box49"][i % 4]
+        if kind in ("heat5r", "box9"):
+            W = inputs.batch_grid_weights(kind, i)
+        else:
+            W = inputs.pattern_weights(kind, stream=2000 + i)
+        boundary = "periodic" if (i % 3 == 2 and nx % 4 == 0) else "zero"
+        T = int(rng.integers(0, 40))
+        x = torch.from_numpy(inputs.field(ny, nx, stream=500 + i)).cuda()
+        grids.append(dict(x=x, out=torch.empty_like(x), weights=W, T=T, boundary=boundary))
+    return grids
+
+
+@pytest.mark.parametrize("tb_depth,threads", [(0, 0), (2, 64), (4, 256), (1, 128)])
+def test_mixed_batch_bitwise_equals_single_runs(oracle, tb_depth, threads):
+    from paper_2605_07954_gb300 import Batch
+    grids = _mixed_grids()
+    b = Batch(grids, tb_depth=tb_depth, threads=threads, tile_rows=(0 if tb_depth else 48))
+    b.run()
+    torch.cuda.synchronize()
+    b.status()
+    info = b.info()
+    assert info["n"] == len(grids) and info["launches"] >= 1
+    for i, g in enumerate(grids):
+        ref = _single(g["x"], g["weights"], g["T"], g["boundary"])
+        assert torch.equal(g["out"], ref), (i, g["x"].shape, g["T"], info)
+        if g["x"].numel() <= 300 * 600:
+            want = oracle.sweep_f64(g["x"].cpu().numpy(), g["weights"], g["T"], g["boundary"])
+            assert rel_l2(g["out"].cpu().numpy(), want) <= fp32_tol(g["T"]), i
+    # the graph replays: a second run gives the same bits
+    first = [g["out"].clone() for g in grids]
+    b.run()
+    torch.cuda.synchronize()
+    for g, f in zip(grids, first):
+        assert torch.equal(g["out"], f)
+    b.close()
+
+
+def test_in_place_grids():
+    from paper_2605_07954_gb300 import Batch
+    W = inputs.batch_grid_weights("box9", 3)
+    x = torch.from_numpy(inputs.field(333, 444)).cuda()
+    ref = _single(x, W, 25, "zero")
+    z = x.clone()
+    b = Batch([dict(x=z, out=z, weights=W, T=25)])
+    b.run()
+    torch.cuda.synchronize()
+    assert torch.equal(z, ref)
+    b.close()
+
+
+def test_withheld_item_times_out_and_reports():
+    """A work item whose completion is never published: the dependent waits run
+    out after timeout_ms, the kernel returns, and the status word says TIMEOUT."""
+    from paper_2605_07954_gb300 import Batch, StencilError
+    W = inputs.batch_grid_weights("box9", 1)
+    x = torch.from_numpy(inputs.field(1024, 1024)).cuda()
+    g = [dict(x=x, out=torch.empty_like(x), weights=W, T=64)]
+    b = Batch(g, tb_depth=8, timeout_ms=200, debug_withhold_item=1)
+    b.run()
+    torch.cuda.synchronize()
+    with pytest.raises(StencilError, match="TIMEOUT"):
+        b.status()
+    b.close()
+    # the device is healthy afterwards: a normal batch runs and is correct
+    b2 = Batch(g, tb_depth=8)
+    b2.run()
+    torch.cuda.synchronize()
+    b2.status()
+    assert torch.equal(g[0]["out"], _single(x, W, 64, "zero"))
+    b2.close()
+
+
+def _workload_256():
+    sides, kinds = inputs.batch_spec(256)
+    grids = []
+    for gi, (s, kind) in enumerate(zip(sides, kinds)):
+        W = inputs.batch_grid_weights(kind, gi)
+        x = torch.from_numpy(inputs.field(int(s), int(s), stream=10000 + gi)).cuda()
+        grids.append(dict(x=x, out=torch.empty_like(x), weights=W, T=200))
+    return grids
+
+
+def test_batched_256_grids_workload(oracle):
+    """The 256-grid, 200-step batch: every grid bit-equal to its single-grid run;
+    the smallest grids also against the FP64 oracle; maximum principle on all."""
+    from paper_2605_07954_gb300 import Batch
+    grids = _workload_256()
+    b = Batch(grids)
+    b.run()
+    torch.cuda.synchronize()
+    b.status()
+    order = sorted(range(len(grids)), key=lambda i: grids[i]["x"].shape[0])
+    for i in range(len(grids)):
+        g = grids[i]
+        out = g["out"]
+        assert float(out.min()) >= 0.0 and float(out.max()) <= float(g["x"].max()) * (1 + 1e-5)
+        if i % 8 == 0 or i in order[:4] or i in order[-2:]:
+            assert torch.equal(out, _single(g["x"], g["weights"], 200, "zero")), i
+    for i in order[:3]:
+        g = grids[i]
+        want = oracle.sweep_f64(g["x"].cpu().numpy(), g["weights"], 200)
+        assert rel_l2(g["out"].cpu().numpy(), want) <= fp32_tol(200)
+    b.close()
