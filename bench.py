@@ -187,6 +187,8 @@ def run_reference(args):
 VARIANTS = {
     "batched": "256 grids, sides log-uniform in [64, 2048], half Heat-5pt / half Box-9pt with random "
                "normalised weights, 200 steps each, FP32, one persistent launch per run (CUDA graph)",
+    "adjoint": "Heat-2D 5-point FP32, 4096x4096, 512 steps: forward sweep + adjoint (dL/du0 and dL/dW "
+               "for L = 0.5||u_T - target||^2) with sqrt(T) checkpointing",
 }
 
 
@@ -255,12 +257,72 @@ def run_variant(args, world, rank, local):
             "clocks": clocks,
         })
         b.close()
+    if name == "adjoint":
+        from paper_2605_07954_gb300 import Plan, adjoint
+        n, T = 4096, 512
+        W = inputs.heat_weights(0.2)
+        h_u0 = torch.from_numpy(inputs.field(n, n)).pin_memory()
+        h_tg = torch.from_numpy(inputs.field(n, n, stream=inputs.STREAM_TARGET)).pin_memory()
+        u0, target = h_u0.cuda(), h_tg.cuda()
+        plan = Plan(n, n, W, autotune=not args.no_autotune)
+        holder = {}
+
+        def fwd():
+            holder["uT"] = plan.run(u0, T)
+
+        def bwd():
+            gT = holder["uT"] - target
+            holder["g"] = adjoint(plan, u0, gT, T)
+
+        def step():
+            fwd()
+            bwd()
+        sampler = ClockSampler(gpu_id)
+        sampler.start()
+        ms = _time_steps(step, args.steps, args.warmup, stream)
+        clocks = sampler.stop()
+        fwd_ms = _time_steps(fwd, args.steps, 1, stream)
+        bwd_ms = _time_steps(bwd, args.steps, 1, stream)
+        plan.status()
+        ms = _max_over_ranks(world, ms)
+
+        def e2e_step():
+            u0.copy_(h_u0, non_blocking=True)
+            target.copy_(h_tg, non_blocking=True)
+            step()
+            gu, gw = holder["g"]
+            gu.cpu()
+            gw.cpu()
+        e2e_ms = _time_steps(e2e_step, max(1, min(args.steps, 3)), 1, stream)
+        launches = plan.launches(T) + int(_capi_launches_adjoint(plan, T))
+        units = float(n) * n * T
+        line.update({
+            "metric": "GStencil/s (Heat-2D FP32 forward + adjoint, 4096^2, 512 steps)",
+            "value": world * units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
+            "dtype": "f32",
+            "config": {"workload": VARIANTS[name], "ny": n, "nx": n, "T": T,
+                       "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+                       "ckpt_interval": int(np.ceil(np.sqrt(T))), "plan": plan.info(),
+                       "l2": "inputs larger than L2 (64 MiB per grid, 23 checkpoints)"},
+            "gpu_launches": launches * args.steps,
+            "e2e": {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GStencil/s",
+                    "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4 + 9 * 8,
+                    "api": "Plan.run + stencil_adjoint (torch copies of pinned host u0/target, "
+                           "gradients read back)"},
+            "clocks": clocks,
+        })
+        plan.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _capi_launches_adjoint(plan, T):
+    from paper_2605_07954_gb300 import _capi
+    return _capi.load().stencil_adjoint_launches(plan.handle, int(T), 0)
 
 
 def main():

@@ -153,6 +153,35 @@ int64_t stencil_run_launches(const stencil_plan_t* plan, int64_t T);
 stencil_status_t stencil_plan_status(stencil_plan_t* plan);
 
 /*
+ * Reverse-mode gradient of T steps (the adjoint of the Sec. II-C update).
+ * For a loss L(u_T) whose gradient at u_T is grad_uT:
+ *     lambda_T = grad_uT,  lambda_t = A^T lambda_{t+1}  (correlation with the
+ *     flipped weights W[-dy][-dx], same boundary rule),
+ *     grad_u0 = lambda_0,
+ *     grad_w[(dy+r)*(2r+1)+(dx+r)] = sum_{t<T} sum_{i,j} lambda_{t+1}[i][j] u~_t[i+dy][j+dx].
+ *   plan           an FP32 plan (other dtypes: STENCIL_ERR_UNSUPPORTED).
+ *   u0, grad_uT    DEVICE, ny*nx FP32, only read.
+ *   grad_u0        DEVICE, ny*nx FP32, written (may equal grad_uT).
+ *   grad_w         DEVICE, (2r+1)^2 FP64, written; NULL to skip.  Every entry of the
+ *                  square is returned, off-footprint ones included.
+ *   ckpt_interval  steps between checkpoints; 0 = ceil(sqrt(T)).  The result does
+ *                  not depend on it (same bits).
+ * States are recomputed from checkpoints, not stored: the plan allocates and
+ * keeps (ceil(T/s) + s + 2) grids of scratch, s = ckpt_interval.  The weight
+ * gradient is reduced deterministically (fixed order, FP64 partials).
+ * Asynchronous on `stream` like stencil_run.
+ */
+stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const void* grad_uT, int64_t T,
+                                 void* grad_u0, double* grad_w, int64_t ckpt_interval,
+                                 stencil_stream_t stream);
+
+/* Kernel launches stencil_adjoint makes for T and ckpt_interval (grad_w != NULL). */
+int64_t stencil_adjoint_launches(const stencil_plan_t* plan, int64_t T, int64_t ckpt_interval);
+
+/* Message for the last failure of stencil_adjoint on the calling thread. */
+const char* stencil_adjoint_last_error(void);
+
+/*
  * ---- Batches: many independent grids in one persistent launch ----------------
  *
  * Each grid of a batch is its own Jacobi problem (Sec. II-C): its own size,

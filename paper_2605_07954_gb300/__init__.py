@@ -111,6 +111,63 @@ class Plan:
         check(_capi.load().stencil_plan_status(self._h), "stencil_plan_status")
 
 
+def adjoint(plan: Plan, u0, grad_uT, T: int, ckpt_interval: int = 0):
+    """(dL/du0, dL/dW) for a loss L(u_T) with dL/du_T = grad_uT (stencil_adjoint).
+
+    Returns a CUDA tensor like u0 and a (2r+1, 2r+1) float64 CUDA tensor.
+    Enqueued on torch's current stream.
+    """
+    import torch
+    plan._check_tensor(u0)
+    plan._check_tensor(grad_uT)
+    g_u0 = torch.empty_like(u0)
+    d = 2 * plan.radius + 1
+    g_w = torch.empty((d, d), dtype=torch.float64, device=u0.device)
+    check(_capi.load().stencil_adjoint(plan.handle, u0.data_ptr(), grad_uT.data_ptr(), int(T),
+                                       g_u0.data_ptr(), g_w.data_ptr(), int(ckpt_interval),
+                                       _current_stream_handle()), "stencil_adjoint")
+    return g_u0, g_w
+
+
+def _stencil_fn():
+    import torch
+
+    class StencilFn(torch.autograd.Function):
+        """u_T = A^T u0 with gradients for u0 and the weights (sqrt(T) checkpointing).
+
+        apply(u0, weights, T, boundary="zero", ckpt_interval=0): u0 a CUDA FP32
+        tensor; weights a (2r+1, 2r+1) tensor on any device (its values are read
+        at forward time).  The weight gradient has the weights' dtype and device.
+        """
+
+        @staticmethod
+        def forward(ctx, u0, weights, T, boundary="zero", ckpt_interval=0):
+            W = weights.detach().to("cpu", torch.float32).numpy()
+            plan = Plan(u0.shape[0], u0.shape[1], W, boundary=boundary)
+            u0c = u0.detach().contiguous()
+            y = plan.run(u0c, int(T))
+            ctx.save_for_backward(u0c)
+            ctx.plan, ctx.T, ctx.ckpt = plan, int(T), int(ckpt_interval)
+            ctx.wdtype, ctx.wdevice = weights.dtype, weights.device
+            return y
+
+        @staticmethod
+        def backward(ctx, grad_y):
+            (u0,) = ctx.saved_tensors
+            g_u0, g_w = adjoint(ctx.plan, u0, grad_y.contiguous(), ctx.T, ctx.ckpt)
+            return g_u0, g_w.to(ctx.wdevice, ctx.wdtype), None, None, None
+
+    return StencilFn
+
+
+def __getattr__(name):
+    if name == "StencilFn":
+        fn = _stencil_fn()
+        globals()["StencilFn"] = fn
+        return fn
+    raise AttributeError(name)
+
+
 class Batch:
     """Many independent grids run by one persistent launch (CUDA-graph replayed).
 
@@ -181,4 +238,4 @@ def run(x, weights, T: int, boundary: str = "zero", **options):
     return y
 
 
-__all__ = ["Plan", "Batch", "run", "StencilError", "DTYPES", "BOUNDARIES"]
+__all__ = ["Plan", "Batch", "StencilFn", "adjoint", "run", "StencilError", "DTYPES", "BOUNDARIES"]

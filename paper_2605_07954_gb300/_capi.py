@@ -74,6 +74,9 @@ _PROTOS = {
     "stencil_status_string": (ctypes.c_char_p, [_i32]),
     "stencil_last_error": (ctypes.c_char_p, []),
     "stencil_version": (_i32, []),
+    "stencil_adjoint": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp]),
+    "stencil_adjoint_launches": (_i64, [_vp, _i64, _i64]),
+    "stencil_adjoint_last_error": (ctypes.c_char_p, []),
     "stencil_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(stencil_grid_desc_t),
                                     _i32, ctypes.POINTER(stencil_batch_options_t)]),
     "stencil_run_batched": (_i32, [_vp, _vp]),
@@ -120,7 +123,9 @@ class StencilError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib = load()
         name = lib.stencil_status_string(status).decode()
-        if "batch" in where:
+        if "adjoint" in where:
+            msg = lib.stencil_adjoint_last_error().decode()
+        elif "batch" in where:
             msg = lib.stencil_batch_last_error().decode()
         elif "noalloc" in where:
             msg = lib.stencil_noalloc_last_error().decode()

@@ -1,0 +1,307 @@
+// adjoint.cu -- reverse-mode gradient of T Jacobi steps (stencil_adjoint).
+//
+// Forward (Sec. II-C): u_{t+1} = A u_t, (A u)[i][j] = sum_{dy,dx} W[dy+R][dx+R] u~[i+dy][j+dx].
+// For a loss L(u_T) with lambda_T = dL/du_T:
+//     lambda_t = A^T lambda_{t+1},  (A^T l)[p][q] = sum_{dy,dx} W[dy+R][dx+R] l~[p-dy][q-dx]
+//              (a correlation with the flipped weights, same boundary rule),
+//     dL/dW[dy+R][dx+R] = sum_{t<T} sum_{i,j} lambda_{t+1}[i][j] u~_t[i+dy][j+dx],
+//     dL/du_0 = lambda_0.
+//
+// Memory: the states u_t are recomputed, not stored: a checkpoint every s
+// steps (s = ceil(sqrt(T)) by default) is written by a temporally blocked
+// forward pass; walking the segments backwards, each segment's s states are
+// recomputed one step per launch from its checkpoint, then the adjoint steps
+// of the segment run from its last state down to its first.  Both forward
+// paths use the same per-point arithmetic, so the result does not depend on s.
+//
+// adjoint_step_kernel fuses, for one step, the lambda update and the
+// weight-gradient products: a CTA stages a 32x32 tile of lambda_{t+1} and of
+// u_t with an R-wide halo in shared memory, writes lambda_t for the tile, and
+// adds the tile's (2R+1)^2 products lambda_{t+1} * shifted(u_t) to a per-tile
+// FP64 partial.  Tile t of a launch is always CTA t and launches are ordered,
+// so each partial sums its steps in a fixed order; a last kernel sums the
+// partials over tiles in a fixed order.  The gradient is deterministic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "../../include/stencil.h"
+#include "common.cuh"
+
+namespace gbst {
+
+// Internal accessors of a plan (plan.cu).
+void plan_weights(const stencil_plan_t* p, float* w);
+void** plan_aux(stencil_plan_t* p, void (**freer)(void*));
+void plan_set_aux_free(stencil_plan_t* p, void (*freer)(void*));
+
+constexpr int kAdjTile = 32;  // output tile side
+constexpr int kAdjRowsPerThread = 4;
+
+template <int R>
+__global__ void __launch_bounds__(256)
+    adjoint_step_kernel(const float* __restrict__ lam_in, const float* __restrict__ u,
+                        float* __restrict__ lam_out, double* __restrict__ partials, int ny, int nx,
+                        int periodic, Weights w, int tiles_x) {
+    constexpr int D = 2 * R + 1;
+    constexpr int S = kAdjTile + 2 * R;  // staged side
+    __shared__ float sl[S][S + 1];
+    __shared__ float su[S][S + 1];
+    __shared__ float red[8][D * D];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // (32, 8)
+    const int tid = ty * 32 + tx;
+    const int x0 = (blockIdx.x % tiles_x) * kAdjTile;
+    const int y0 = (blockIdx.x / tiles_x) * kAdjTile;
+
+    // Stage both tiles with their halo (zero outside, or wrapped).
+    for (int i = tid; i < S * S; i += 256) {
+        const int r = i / S, c = i % S;
+        int y = y0 - R + r, x = x0 - R + c;
+        float a = 0.f, b = 0.f;
+        if (periodic) {
+            y = (y % ny + ny) % ny;
+            x = (x % nx + nx) % nx;
+            a = lam_in[(size_t)y * nx + x];
+            b = u[(size_t)y * nx + x];
+        } else if (y >= 0 && y < ny && x >= 0 && x < nx) {
+            a = lam_in[(size_t)y * nx + x];
+            b = u[(size_t)y * nx + x];
+        }
+        sl[r][c] = a;
+        su[r][c] = b;
+    }
+    __syncthreads();
+
+    float g[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) g[k] = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < kAdjRowsPerThread; ++rr) {
+        const int ly = ty + 8 * rr, lx = tx;
+        const int y = y0 + ly, x = x0 + lx;
+        if (y >= ny || x >= nx) continue;
+        // lambda_t[p] = sum_d W[d] lambda_{t+1}[p - d], dy-major then dx
+        float acc = 0.f;
+#pragma unroll
+        for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx)
+                acc = fmaf(w.w[(dy + R) * D + (dx + R)], sl[ly + R - dy][lx + R - dx], acc);
+        lam_out[(size_t)y * nx + x] = acc;
+        // dL/dW[d] += lambda_{t+1}[p] * u_t[p + d]
+        const float lp = sl[ly + R][lx + R];
+#pragma unroll
+        for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx)
+                g[(dy + R) * D + (dx + R)] =
+                    fmaf(lp, su[ly + R + dy][lx + R + dx], g[(dy + R) * D + (dx + R)]);
+    }
+    // Fixed-order reduction: butterfly within each warp, then warps in order.
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) {
+        float v = g[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (tx == 0) red[ty][k] = v;
+    }
+    __syncthreads();
+    if (tid < D * D) {
+        double s = 0.0;
+        for (int wv = 0; wv < 8; ++wv) s += (double)red[wv][tid];
+        partials[(size_t)blockIdx.x * D * D + tid] += s;
+    }
+}
+
+// grad_w[k] = sum over tiles of partials[tile][k], tiles in increasing order.
+__global__ void reduce_partials_kernel(const double* __restrict__ partials, int tiles, int taps,
+                                       double* __restrict__ grad_w) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= taps) return;
+    double s = 0.0;
+    for (int t = 0; t < tiles; ++t) s += partials[(size_t)t * taps + k];
+    grad_w[k] = s;
+}
+
+static const void* adjoint_kernel(int R) {
+    switch (R) {
+        case 1: return (const void*)adjoint_step_kernel<1>;
+        case 2: return (const void*)adjoint_step_kernel<2>;
+        case 3: return (const void*)adjoint_step_kernel<3>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace gbst
+
+using namespace gbst;
+
+namespace {
+
+thread_local std::string g_adj_error;
+
+stencil_status_t afail(stencil_status_t st, const std::string& msg) {
+    g_adj_error = msg;
+    return st;
+}
+
+#define ACK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return afail(STENCIL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device scratch of the adjoint, kept by the plan and grown on demand.
+struct AdjScratch {
+    float* base = nullptr;
+    size_t grids = 0;
+    double* partials = nullptr;
+    size_t npartials = 0;
+};
+
+void adj_scratch_free(void* v) {
+    AdjScratch* sc = static_cast<AdjScratch*>(v);
+    if (sc->base) cudaFree(sc->base);
+    if (sc->partials) cudaFree(sc->partials);
+    delete sc;
+}
+
+stencil_status_t adj_scratch(stencil_plan_t* plan, size_t grids, size_t grid_bytes, size_t npartials,
+                             AdjScratch** out) {
+    void (*freer)(void*) = nullptr;
+    void** slot = plan_aux(plan, &freer);
+    AdjScratch* sc = static_cast<AdjScratch*>(*slot);
+    if (!sc) {
+        sc = new (std::nothrow) AdjScratch();
+        if (!sc) return afail(STENCIL_ERR_OOM, "host allocation failed");
+        *slot = sc;
+        plan_set_aux_free(plan, adj_scratch_free);
+    }
+    if (sc->grids < grids) {
+        if (sc->base) cudaFree(sc->base);
+        sc->base = nullptr;
+        sc->grids = 0;
+        if (cudaMalloc(&sc->base, grids * grid_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            sc->base = nullptr;
+            return afail(STENCIL_ERR_OOM, "cudaMalloc of " + std::to_string(grids) + " adjoint grids failed");
+        }
+        sc->grids = grids;
+    }
+    if (sc->npartials < npartials) {
+        if (sc->partials) cudaFree(sc->partials);
+        sc->partials = nullptr;
+        sc->npartials = 0;
+        if (cudaMalloc(&sc->partials, sizeof(double) * npartials) != cudaSuccess) {
+            cudaGetLastError();
+            sc->partials = nullptr;
+            return afail(STENCIL_ERR_OOM, "cudaMalloc of the gradient partials failed");
+        }
+        sc->npartials = npartials;
+    }
+    *out = sc;
+    return STENCIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stencil_adjoint_last_error(void) { return g_adj_error.c_str(); }
+
+stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const void* grad_uT, int64_t T,
+                                 void* grad_u0, double* grad_w, int64_t ckpt_interval,
+                                 stencil_stream_t stream) {
+    if (!plan || !u0 || !grad_uT || !grad_u0) return afail(STENCIL_ERR_INVALID_ARG, "NULL argument");
+    if (T < 0 || ckpt_interval < 0) return afail(STENCIL_ERR_INVALID_ARG, "T and ckpt_interval must be >= 0");
+    stencil_plan_info_t info{};
+    stencil_status_t s = stencil_plan_info(plan, &info);
+    if (s != STENCIL_OK) return afail(s, "stencil_plan_info failed");
+    if (info.dtype != STENCIL_F32) return afail(STENCIL_ERR_UNSUPPORTED, "the adjoint supports FP32 plans only");
+    const int R = info.radius, D = 2 * R + 1;
+    const int ny = (int)info.ny, nx = (int)info.nx;
+    const size_t n = (size_t)ny * (size_t)nx;
+    const size_t bytes = n * sizeof(float);
+    cudaStream_t st = (cudaStream_t)stream;
+    Weights wf{};
+    plan_weights(plan, wf.w);
+    Weights wadj = wf;  // the step kernel indexes W directly; flip is in its loop
+
+    const int tiles_x = (nx + kAdjTile - 1) / kAdjTile;
+    const int tiles = tiles_x * ((ny + kAdjTile - 1) / kAdjTile);
+    if (T == 0) {
+        if (grad_u0 != grad_uT) ACK(cudaMemcpyAsync(grad_u0, grad_uT, bytes, cudaMemcpyDeviceToDevice, st));
+        if (grad_w) ACK(cudaMemsetAsync(grad_w, 0, sizeof(double) * D * D, st));
+        return STENCIL_OK;
+    }
+    const int64_t sgm = ckpt_interval > 0 ? std::min<int64_t>(ckpt_interval, T)
+                                          : (int64_t)std::ceil(std::sqrt((double)T));
+    const int64_t nseg = (T + sgm - 1) / sgm;
+    // Buffers: nseg checkpoints, sgm segment states, two adjoint grids.
+    AdjScratch* sc = nullptr;
+    const size_t grids = (size_t)nseg + (size_t)sgm + 2;
+    s = adj_scratch(plan, grids, bytes, (size_t)tiles * D * D, &sc);
+    if (s != STENCIL_OK) return s;
+    float* ckpt = sc->base;
+    float* seg = sc->base + (size_t)nseg * n;
+    float* lam[2] = {sc->base + (size_t)(nseg + sgm) * n, sc->base + (size_t)(nseg + sgm + 1) * n};
+    double* partials = sc->partials;
+    ACK(cudaMemsetAsync(partials, 0, sizeof(double) * (size_t)tiles * D * D, st));
+
+    // Checkpoints u_{j*sgm}, j = 0..nseg-1 (temporally blocked forward).
+    ACK(cudaMemcpyAsync(ckpt, u0, bytes, cudaMemcpyDeviceToDevice, st));
+    for (int64_t j = 1; j < nseg; ++j) {
+        s = stencil_run(plan, ckpt + (size_t)(j - 1) * n, ckpt + (size_t)j * n, sgm, stream);
+        if (s != STENCIL_OK) return afail(s, std::string("checkpoint pass: ") + stencil_last_error());
+    }
+    ACK(cudaMemcpyAsync(lam[0], grad_uT, bytes, cudaMemcpyDeviceToDevice, st));
+    int cur = 0;
+    const void* kfn = adjoint_kernel(R);
+    if (!kfn) return afail(STENCIL_ERR_UNSUPPORTED, "no adjoint kernel for this radius");
+    int periodic = info.boundary == STENCIL_BOUNDARY_PERIODIC;
+    for (int64_t j = nseg - 1; j >= 0; --j) {
+        const int64_t t0 = j * sgm;
+        const int64_t len = std::min<int64_t>(sgm, T - t0);
+        // states u_{t0} .. u_{t0+len-1}: seg[0] is the checkpoint itself
+        const float* state0 = ckpt + (size_t)j * n;
+        for (int64_t t = 1; t < len; ++t) {
+            const float* src = t == 1 ? state0 : seg + (size_t)(t - 1) * n;
+            s = stencil_run(plan, src, seg + (size_t)t * n, 1, stream);
+            if (s != STENCIL_OK) return afail(s, std::string("segment recompute: ") + stencil_last_error());
+        }
+        for (int64_t t = len - 1; t >= 0; --t) {
+            const float* ut = t == 0 ? state0 : seg + (size_t)t * n;
+            const float* lin = lam[cur];
+            float* lout = lam[cur ^ 1];
+            void* args[] = {(void*)&lin, (void*)&ut, (void*)&lout, (void*)&partials,
+                            (void*)&ny, (void*)&nx, (void*)&periodic, (void*)&wadj, (void*)&tiles_x};
+            ACK(cudaLaunchKernel(kfn, dim3((unsigned)tiles), dim3(32, 8), args, 0, st));
+            cur ^= 1;
+        }
+    }
+    ACK(cudaMemcpyAsync(grad_u0, lam[cur], bytes, cudaMemcpyDeviceToDevice, st));
+    if (grad_w) {
+        const int taps = D * D;
+        reduce_partials_kernel<<<1, 64, 0, st>>>(partials, tiles, taps, grad_w);
+        ACK(cudaGetLastError());
+    }
+    return STENCIL_OK;
+}
+
+int64_t stencil_adjoint_launches(const stencil_plan_t* plan, int64_t T, int64_t ckpt_interval) {
+    if (!plan || T < 0 || ckpt_interval < 0) return -1;
+    if (T == 0) return 0;
+    const int64_t sgm = ckpt_interval > 0 ? std::min<int64_t>(ckpt_interval, T)
+                                          : (int64_t)std::ceil(std::sqrt((double)T));
+    const int64_t nseg = (T + sgm - 1) / sgm;
+    int64_t L = (nseg - 1) * stencil_run_launches(plan, sgm);  // checkpoints
+    L += (T - nseg);                                            // segment recompute, 1 step each
+    L += T;                                                     // adjoint steps
+    return L + 1;                                               // reduction
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+"""GPU tests of the adjoint (stencil_adjoint) and the autograd Function.
+
+The adjoint is checked against the FP64 oracle's gradient (which the CPU pins
+check against finite differences), by the dot test <A^T x, y> = <x, (A^T)' y>,
+and for exact independence of the checkpoint interval.
+"""
+import numpy as np
+import pytest
+
+from paper_2605_07954_gb300 import inputs
+from _util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_07954_gb300 import build
+    build.build()
+
+
+def _grads(u0, W, T, gT, boundary="zero", ckpt=0, **plan_opts):
+    from paper_2605_07954_gb300 import Plan, adjoint
+    p = Plan(u0.shape[0], u0.shape[1], W, boundary=boundary, **plan_opts)
+    gu, gw = adjoint(p, torch.from_numpy(np.ascontiguousarray(u0, dtype=np.float32)).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(gT, dtype=np.float32)).cuda(), T, ckpt)
+    torch.cuda.synchronize()
+    p.close()
+    return gu.cpu().numpy().astype(np.float64), gw.cpu().numpy()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "periodic"])
+@pytest.mark.parametrize("name", ["heat5", "box9", "star13", "asym2"])
+def test_gradients_match_oracle(oracle, name, boundary):
+    """64x64, 32 steps, L = 0.5 ||u_T - target||^2: both gradients vs the FP64 oracle."""
+    if name == "asym2":
+        rng = np.random.default_rng(41)
+        W = (rng.uniform(-1, 1, size=(5, 5)) / 12.5).astype(np.float32)
+    else:
+        W = inputs.pattern_weights(name)
+    u0 = inputs.field(64, 64)
+    target = inputs.field(64, 64, stream=inputs.STREAM_TARGET)
+    T = 32
+    uT = oracle.sweep_f64(u0, W, T, boundary)
+    gT = (uT - target).astype(np.float32)
+    ref_u, ref_w = oracle.adjoint_f64(u0, W, T, gT.astype(np.float64), boundary)
+    gu, gw = _grads(u0, W, T, gT, boundary)
+    assert rel_l2(gu, ref_u) <= 1e-4
+    fp = np.abs(W) > 0
+    assert rel_l2(gw[fp], ref_w[fp]) <= 1e-4
+    assert rel_l2(gw, ref_w) <= 1e-4
+
+
+def test_checkpoint_interval_does_not_change_bits():
+    W = inputs.pattern_weights("box9")
+    u0 = inputs.field(100, 130)
+    gT = inputs.field(100, 130, stream=inputs.STREAM_TARGET)
+    T = 37
+    base = _grads(u0, W, T, gT, ckpt=0)
+    for c in (1, 5, 36, 37, 100):
+        other = _grads(u0, W, T, gT, ckpt=c)
+        assert np.array_equal(base[0], other[0]) and np.array_equal(base[1], other[1]), c
+    # and neither on the forward plan's temporal-blocking depth
+    for k in (1, 2, 8):
+        other = _grads(u0, W, T, gT, tb_depth=k)
+        assert np.array_equal(base[0], other[0]) and np.array_equal(base[1], other[1]), k
+
+
+@pytest.mark.parametrize("boundary", ["zero", "periodic"])
+def test_dot_test(boundary):
+    """<A^T x, y> = <x, (A^T)' y> for the T-step operator, in FP32 to 1e-5."""
+    from paper_2605_07954_gb300 import Plan
+    rng = np.random.default_rng(43)
+    W = (rng.uniform(-1, 1, size=(7, 7)) / 20).astype(np.float32)
+    x = rng.normal(size=(300, 257)).astype(np.float32)
+    y = rng.normal(size=(300, 257)).astype(np.float32)
+    T = 20
+    p = Plan(300, 257, W, boundary=boundary)
+    Ax = p.run(torch.from_numpy(x).cuda(), T).cpu().numpy().astype(np.float64)
+    p.close()
+    ATy, _ = _grads(np.zeros_like(x), W, T, y, boundary)
+    lhs, rhs = float(np.vdot(Ax, y)), float(np.vdot(x.astype(np.float64), ATy))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), np.linalg.norm(Ax) * np.linalg.norm(y) * 1e-3)
+
+
+def test_autograd_function_matches_adjoint(oracle):
+    from paper_2605_07954_gb300 import StencilFn
+    W = torch.from_numpy(inputs.heat_weights(0.2).astype(np.float64)).requires_grad_()
+    u0 = torch.from_numpy(inputs.field(64, 64)).cuda().requires_grad_()
+    target = torch.from_numpy(inputs.field(64, 64, stream=inputs.STREAM_TARGET)).cuda()
+    uT = StencilFn.apply(u0, W, 32)
+    loss = 0.5 * ((uT - target) ** 2).sum()
+    loss.backward()
+    gT = (uT.detach() - target).cpu().numpy().astype(np.float64)
+    ref_u, ref_w = oracle.adjoint_f64(u0.detach().cpu().numpy(), W.detach().numpy(), 32, gT)
+    assert rel_l2(u0.grad.cpu().numpy(), ref_u) <= 1e-4
+    assert W.grad.dtype == torch.float64 and W.grad.device.type == "cpu"
+    assert rel_l2(W.grad.numpy(), ref_w) <= 1e-4
+
+
+def test_fullsize_heat_4096_T512_window(oracle):
+    """The 4096^2, 512-step Heat workload: the corner window of dL/du0 against
+    the FP64 oracle on its exact light cone, and the dot test at full size."""
+    from paper_2605_07954_gb300 import Plan, adjoint
+    n, T = 4096, 512
+    W = inputs.heat_weights(0.2)
+    u0 = inputs.field(n, n)
+    target = inputs.field(n, n, stream=inputs.STREAM_TARGET)
+    p = Plan(n, n, W)
+    x = torch.from_numpy(u0).cuda()
+    uT = p.run(x, T)
+    gT = uT - torch.from_numpy(target).cuda()
+    gu, gw = adjoint(p, x, gT, T)
+    torch.cuda.synchronize()
+    # window [0, b)^2 of lambda_0 needs lambda_T on [0, b + T), which needs u_0 on [0, b + 2T)
+    b = 24
+    m1, m2 = b + T, b + 2 * T
+    uT_ref = oracle.sweep_f64(u0[:m2, :m2], W, T)[:m1, :m1]
+    gT_ref = uT_ref - target[:m1, :m1]
+    lam0_ref, _ = oracle.adjoint_f64(np.zeros((m1, m1)), W, T, gT_ref)
+    e = rel_l2(gu[:b, :b].cpu().numpy(), lam0_ref[:b, :b])
+    print(f"4096^2 T=512 corner window dL/du0 relL2={e:.3e}")
+    assert e <= 1e-4
+    # dot test of the full-size operator: <A^T x, y> = <x, (A^T)' y>
+    yv = gT
+    Ax = uT
+    zero = torch.zeros_like(x)
+    ATy, _ = adjoint(p, zero, yv, T)
+    lhs = float(torch.dot(Ax.double().flatten(), yv.double().flatten()))
+    rhs = float(torch.dot(x.double().flatten(), ATy.double().flatten()))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    p.close()
