@@ -189,6 +189,22 @@ VARIANTS = {
                "normalised weights, 200 steps each, FP32, one persistent launch per run (CUDA graph)",
     "adjoint": "Heat-2D 5-point FP32, 4096x4096, 512 steps: forward sweep + adjoint (dL/du0 and dL/dW "
                "for L = 0.5||u_T - target||^2) with sqrt(T) checkpointing",
+    "box49": "Box-2D49P, 16384x16384, 200 steps, FP32 storage, FP32 CUDA-core arithmetic",
+    "box49-bf16": "Box-2D49P, 16384x16384, 200 steps, BF16 storage, FP32 CUDA-core arithmetic",
+    "box49-tc-tf32": "Box-2D49P, 16384x16384, 200 steps, FP32 storage, TF32 tensor-core contraction, FP32 accumulate",
+    "box49-tc-bf16": "Box-2D49P, 16384x16384, 200 steps, BF16 storage, BF16 tensor-core contraction, FP32 accumulate",
+    "box9+star13-bf16": "Box-2D9P and Star-2D13P, 8192x8192, 1000 steps each, BF16 storage, FP32 arithmetic",
+    "heat512": "Heat-2D 5-point (weights 0.2f), 512x512, 100 steps, FP32, zero boundary",
+}
+
+# (pattern list, n, T, dtype, compute) of the single-plan variants
+_PLAN_VARIANTS = {
+    "box49": (("box49",), 16384, 200, "f32", "fp32"),
+    "box49-bf16": (("box49",), 16384, 200, "bf16", "fp32"),
+    "box49-tc-tf32": (("box49",), 16384, 200, "f32", "tc_tf32"),
+    "box49-tc-bf16": (("box49",), 16384, 200, "bf16", "tc_bf16"),
+    "box9+star13-bf16": (("box9", "star13"), 8192, 1000, "bf16", "fp32"),
+    "heat512": (("heat5",), 512, 100, "f32", "fp32"),
 }
 
 
@@ -257,6 +273,68 @@ def run_variant(args, world, rank, local):
             "clocks": clocks,
         })
         b.close()
+    if name in _PLAN_VARIANTS:
+        from paper_2605_07954_gb300 import Plan
+        pats, n, T, dtype, compute = _PLAN_VARIANTS[name]
+        tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+        esz = 4 if dtype == "f32" else 2
+        plans, xs, outs, hins, houts = {}, {}, {}, {}, {}
+        for pn in pats:
+            f = inputs.field(n, n)
+            plans[pn] = Plan(n, n, inputs.pattern_weights(pn), dtype=dtype, compute=compute,
+                             autotune=(compute == "fp32" and not args.no_autotune))
+            hins[pn] = torch.from_numpy(f).to(tdt).pin_memory()
+            xs[pn] = hins[pn].cuda()
+            outs[pn] = torch.empty_like(xs[pn])
+            houts[pn] = torch.empty_like(hins[pn]).pin_memory()
+
+        def step():
+            for pn in pats:
+                plans[pn].run(xs[pn], T, out=outs[pn])
+        sampler = ClockSampler(gpu_id)
+        sampler.start()
+        ms = _time_steps(step, args.steps, args.warmup, stream)
+        clocks = sampler.stop()
+        per = {pn: _time_steps(lambda pn=pn: plans[pn].run(xs[pn], T, out=outs[pn]), args.steps, 1, stream)
+               for pn in pats}
+        for pn in pats:
+            plans[pn].status()
+        ms = _max_over_ranks(world, ms)
+
+        def e2e_step():
+            for pn in pats:
+                xs[pn].copy_(hins[pn], non_blocking=True)
+                plans[pn].run(xs[pn], T, out=outs[pn])
+                houts[pn].copy_(outs[pn], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e2e_ms = _time_steps(e2e_step, max(1, min(args.steps, 3)), 1, stream)
+        units = float(len(pats)) * n * n * T
+        peaks, _ = _peaks()
+        info0 = plans[pats[0]].info()
+        k = info0["tb_depth"]
+        launch_ms = per[pats[0]] / plans[pats[0]].launches(T)
+        alg_bytes = 2.0 * esz * n * n * k
+        line.update({
+            "metric": f"GStencil/s ({name}: {', '.join(pats)}, {n}^2, {T} steps)",
+            "value": world * units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
+            "dtype": dtype,
+            "config": {"workload": VARIANTS[name], "ny": n, "nx": n, "T": T, "compute": compute,
+                       "per_pattern_ms": per, "plans": {pn: plans[pn].info() for pn in pats},
+                       "l2": "inputs larger than L2" if n * n * esz > 129e6 else
+                             "grid fits in L2 (parity workload; not roofline-meaningful)"},
+            "gpu_launches": sum(plans[pn].launches(T) for pn in pats) * args.steps,
+            "roofline_hbm_effective": {"achieved_gbs": alg_bytes / (launch_ms * 1e-3) / 1e9,
+                                       "peak_gbs": peaks["hbm_gbs"],
+                                       "frac": alg_bytes / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                       "note": f"{2 * esz} B per point-step x {k} steps per launch "
+                                               f"({pats[0]})"},
+            "e2e": {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GStencil/s",
+                    "h2d_bytes_per_step": len(pats) * n * n * esz, "d2h_bytes_per_step": len(pats) * n * n * esz,
+                    "api": "Plan.run (stencil_run) with torch copies of pinned host grids"},
+            "clocks": clocks,
+        })
+        for pn in pats:
+            plans[pn].close()
     if name == "adjoint":
         from paper_2605_07954_gb300 import Plan, adjoint
         n, T = 4096, 512

@@ -59,8 +59,12 @@ typedef enum { STENCIL_F32 = 0, STENCIL_BF16 = 1, STENCIL_F16 = 2 } stencil_dtyp
 
 typedef enum { STENCIL_BOUNDARY_ZERO = 0, STENCIL_BOUNDARY_PERIODIC = 1 } stencil_boundary_t;
 
-/* Arithmetic engine.  AUTO and FP32 use the CUDA cores; the tensor-core
- * engines apply to the full 7x7 box (radius 3) only. */
+/* Arithmetic engine.  AUTO and FP32 use the CUDA cores.  The tensor-core
+ * engines treat each weight row of a radius-3 (7x7) stencil as a banded
+ * Toeplitz matrix and run the step as warp MMAs with FP32 accumulation
+ * (Sec. II-D's stencil-as-matrix-product idea): TC_TF32 rounds inputs and
+ * weights to TF32, TC_BF16 to BF16 (both round-to-nearest-even).  Storage
+ * FP32 or BF16.  Other radii or FP16 storage: STENCIL_ERR_UNSUPPORTED. */
 typedef enum {
     STENCIL_COMPUTE_AUTO = 0,
     STENCIL_COMPUTE_FP32 = 1,
@@ -72,7 +76,8 @@ typedef enum {
 typedef enum {
     STENCIL_KERNEL_AUTO = 0,
     STENCIL_KERNEL_NAIVE = 1,      /* one thread per point, one step per launch      */
-    STENCIL_KERNEL_STREAM = 2      /* row-streaming tiles, k steps per launch        */
+    STENCIL_KERNEL_STREAM = 2,     /* row-streaming tiles, k steps per launch        */
+    STENCIL_KERNEL_TC = 3          /* tensor-core contraction (7x7 box), 1 step/launch */
 } stencil_kernel_t;
 
 /* Optional plan settings; pass NULL for defaults.  0 means "choose". */

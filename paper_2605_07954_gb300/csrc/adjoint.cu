@@ -221,7 +221,8 @@ stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const voi
     stencil_plan_info_t info{};
     stencil_status_t s = stencil_plan_info(plan, &info);
     if (s != STENCIL_OK) return afail(s, "stencil_plan_info failed");
-    if (info.dtype != STENCIL_F32) return afail(STENCIL_ERR_UNSUPPORTED, "the adjoint supports FP32 plans only");
+    if (info.dtype != STENCIL_F32 || info.compute != STENCIL_COMPUTE_FP32)
+        return afail(STENCIL_ERR_UNSUPPORTED, "the adjoint supports FP32 CUDA-core plans only");
     const int R = info.radius, D = 2 * R + 1;
     const int ny = (int)info.ny, nx = (int)info.nx;
     const size_t n = (size_t)ny * (size_t)nx;

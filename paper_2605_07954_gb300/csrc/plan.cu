@@ -31,6 +31,20 @@ GBST_DECL_STREAM(2, f32) GBST_DECL_STREAM(2, bf16) GBST_DECL_STREAM(2, f16)
 GBST_DECL_STREAM(3, f32) GBST_DECL_STREAM(3, bf16) GBST_DECL_STREAM(3, f16)
 #undef GBST_DECL_STREAM
 const void* get_naive_kernel(int radius, int dtype);
+const void* get_box49_tc_kernel(int dtype, int bf16mma);
+const void* get_box49_tc_pipe_kernel(int dtype, int bf16mma);
+int box49_tc_smem_bytes(int bf16mma);
+struct TcParams {  // must match box49_tc.cu
+    const void* in;
+    void* out;
+    int ny, nx, ld;
+    int periodic;
+    int tiles_x, tiles;
+    int vec;
+    int convert_in;
+    int round_out;
+    float w[49];
+};
 }  // namespace gbst
 
 using namespace gbst;
@@ -62,6 +76,8 @@ struct stencil_plan {
     int kernel = STENCIL_KERNEL_STREAM;
     int k = 1, threads = 0, H = 0, bx = 0, by = 0, strips = 0, tiles_y = 0, smem = 0;
     int per_sm = 0;
+    const void* tc_pipe = nullptr;  // persistent double-buffered tensor-core kernel
+    int tc_pipe_smem = 0, tc_pipe_ctas = 0;
     unsigned smem_set = 0;  // bit 2k+vec: that kernel's shared-memory attribute is set
     int tuned = 0;
     const void* naive = nullptr;
@@ -193,6 +209,37 @@ static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, in
     return STENCIL_OK;
 }
 
+static stencil_status_t configure_tc(stencil_plan* p) {
+    if (p->R != 3) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engines need radius 3 (7x7 weights)");
+    if (p->dtype == STENCIL_F16) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engines take FP32 or BF16 storage");
+    const int bf16 = p->compute == STENCIL_COMPUTE_TC_BF16;
+    p->naive = get_box49_tc_kernel(p->dtype, bf16);
+    if (!p->naive) return fail(STENCIL_ERR_UNSUPPORTED, "no tensor-core kernel for this dtype");
+    p->kernel = STENCIL_KERNEL_TC;
+    p->k = 1;
+    p->threads = 256;
+    p->H = 3;
+    p->bx = 128;
+    p->by = 128;
+    p->strips = (int)ceil_div(p->nx, 128);
+    p->tiles_y = (int)ceil_div(p->ny, 128);
+    p->smem = box49_tc_smem_bytes(bf16);
+    CK(cudaFuncSetAttribute(p->naive, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem));
+    p->tc_pipe = p->nx % 4 == 0 ? get_box49_tc_pipe_kernel(p->dtype, bf16) : nullptr;
+    if (p->tc_pipe) {
+        p->tc_pipe_smem = 2 * p->smem;
+        CK(cudaFuncSetAttribute(p->tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc_pipe_smem));
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->tc_pipe, 256, p->tc_pipe_smem));
+        if (per_sm < 1) {
+            p->tc_pipe = nullptr;
+        } else {
+            p->tc_pipe_ctas = (int)std::min<int64_t>((int64_t)per_sm * p->sms, (int64_t)p->strips * p->tiles_y);
+        }
+    }
+    return STENCIL_OK;
+}
+
 static stencil_status_t configure_naive(stencil_plan* p) {
     p->naive = get_naive_kernel(p->R, p->dtype);
     if (!p->naive) return fail(STENCIL_ERR_UNSUPPORTED, "no naive kernel for this radius");
@@ -208,9 +255,35 @@ static stencil_status_t configure_naive(stencil_plan* p) {
     return STENCIL_OK;
 }
 
-// One launch advancing `nlev` steps from src to dst.
+// One launch advancing `nlev` steps from src to dst.  `first` / `last`: this
+// launch starts / ends a run (the pipelined TF32 engine rounds its input on
+// the first launch and keeps intermediate states TF32-rounded until the last).
 static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst, int nlev,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, int first = 1, int last = 1) {
+    if (p->kernel == STENCIL_KERNEL_TC) {
+        TcParams tp{};
+        tp.in = src;
+        tp.out = dst;
+        tp.ny = (int)p->ny;
+        tp.nx = (int)p->nx;
+        tp.ld = (int)p->nx;
+        tp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+        tp.tiles_x = p->strips;
+        tp.tiles = p->strips * p->tiles_y;
+        tp.vec = (p->nx % 4 == 0) && ((uintptr_t)src % (4 * p->elem) == 0) &&
+                 ((uintptr_t)dst % (4 * p->elem) == 0);
+        tp.convert_in = first;
+        tp.round_out = !last;
+        for (int i = 0; i < 49; ++i) tp.w[i] = p->w.w[i];
+        void* args[] = {&tp};
+        if (p->tc_pipe && tp.vec) {
+            CK(cudaLaunchKernel(p->tc_pipe, dim3((unsigned)p->tc_pipe_ctas), dim3(256), args,
+                                (size_t)p->tc_pipe_smem, st));
+        } else {
+            CK(cudaLaunchKernel(p->naive, dim3((unsigned)tp.tiles), dim3(256), args, (size_t)p->smem, st));
+        }
+        return STENCIL_OK;
+    }
     if (p->kernel == STENCIL_KERNEL_NAIVE) {
         dim3 block(32, 8), grid((unsigned)p->strips, (unsigned)p->tiles_y);
         long long ny = p->ny, nx = p->nx;
@@ -250,11 +323,11 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
 // split greedily into instantiated depths.
 static std::vector<int> launch_depths(const stencil_plan* p, int64_t T) {
     std::vector<int> d;
-    const int k = p->kernel == STENCIL_KERNEL_NAIVE ? 1 : p->k;
+    const int k = p->kernel == STENCIL_KERNEL_STREAM ? p->k : 1;
     for (int64_t t = 0; t < T / k; ++t) d.push_back(k);
     int rem = (int)(T % k);
     while (rem > 0) {
-        const int step = p->kernel == STENCIL_KERNEL_NAIVE ? 1 : stream_depth_at_most(p->R, p->star, rem);
+        const int step = p->kernel == STENCIL_KERNEL_STREAM ? stream_depth_at_most(p->R, p->star, rem) : 1;
         d.push_back(step);
         rem -= step;
     }
@@ -368,10 +441,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     stencil_options_t o{};
     if (opt) o = *opt;
     if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_BF16 || o.kernel < 0 ||
-        o.kernel > STENCIL_KERNEL_STREAM || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0)
+        o.kernel > STENCIL_KERNEL_TC || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0)
         return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
-    if (o.compute == STENCIL_COMPUTE_TC_TF32 || o.compute == STENCIL_COMPUTE_TC_BF16)
-        return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engine not available in this build");
 
     stencil_plan* p = new (std::nothrow) stencil_plan();
     if (!p) return fail(STENCIL_ERR_OOM, "host allocation failed");
@@ -380,7 +451,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     p->R = radius;
     p->dtype = dtype;
     p->boundary = boundary;
-    p->compute = STENCIL_COMPUTE_FP32;
+    p->compute = (o.compute == STENCIL_COMPUTE_TC_TF32 || o.compute == STENCIL_COMPUTE_TC_BF16)
+                     ? o.compute : STENCIL_COMPUTE_FP32;
     p->opt = o;
     p->elem = elem_size(dtype);
     const int D = 2 * radius + 1;
@@ -413,7 +485,10 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     }
 
     stencil_status_t st;
-    if (o.kernel == STENCIL_KERNEL_NAIVE) {
+    if (p->compute != STENCIL_COMPUTE_FP32 || o.kernel == STENCIL_KERNEL_TC) {
+        if (p->compute == STENCIL_COMPUTE_FP32) p->compute = STENCIL_COMPUTE_TC_TF32;
+        st = configure_tc(p);
+    } else if (o.kernel == STENCIL_KERNEL_NAIVE) {
         st = configure_naive(p);
     } else {
         const int k = o.tb_depth > 0 ? o.tb_depth : default_depth(radius, star);
@@ -515,7 +590,7 @@ stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64
     for (size_t i = 0; i < L; ++i) {
         // Launch i (0-based) writes `out` when L-1-i is even, else the workspace.
         void* dst = ((L - 1 - i) % 2 == 0) ? out : p->ws;
-        stencil_status_t s = launch_once(p, src, dst, depths[i], st);
+        stencil_status_t s = launch_once(p, src, dst, depths[i], st, i == 0, i + 1 == L);
         if (s != STENCIL_OK) return s;
         src = dst;
     }
