@@ -12,7 +12,10 @@
 // down the rows from y0 - R*K to y0 + by - 1 + R*K.
 //
 // Each thread owns 4 adjacent columns, held as two column pairs so that the
-// arithmetic runs as packed FP32x2 FMAs (one instruction, two FMAs).  Time
+// arithmetic runs as packed FP32x2 FMAs (one instruction, two FMAs): (c0, c2)
+// and (c1, c3) for radius 1 (every own-column operand is then a register pair
+// as it stands), (c0, c1) and (c2, c3) for radius 2 and 3 (measured faster
+// there).  Time
 // level l+1 is produced from level l as a pipeline along y: when row y of
 // level l arrives it is the last contribution to output row y-R of level l+1
 // and the first to row y+R.  A thread keeps 2R+1 partial sums per column and
@@ -146,12 +149,19 @@ __device__ __forceinline__ void load_chunk_scalar(const StreamParams& p, int y, 
 }
 
 // ---- arithmetic -----------------------------------------------------------------
+//
+// Column pairs.  A thread's 4 columns c0..c3 are held as P0 = (c0, c2) and
+// P1 = (c1, c3), and its outputs as A0 = (o0, o2), A1 = (o1, o3).  The weight
+// (dy, dx) then updates pair q from the source pair (c[q+dx], c[q+dx+2]): for
+// q+dx in {0, 1} that is P0 or P1 itself, so every own-column product takes its
+// operands straight from registers; only the pairs that straddle a neighbour's
+// columns are assembled.  A completed output pair is directly the next level's
+// input pair.
 
-// Own-column products of one arriving row: pair q holds columns 2q, 2q+1.
-// cur2[0] = (c0,c1), cur2[1] = (c2,c3); mid = (c1,c2).
+// Own-column products of one arriving row into the 2R+1 partial sums.
 template <int R, bool STAR, class WS>
-__device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 1][2],
-                                             const float2 (&cur2)[2], float2 mid, int j) {
+__device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 1][2], float2 P0,
+                                             float2 P1, int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
     for (int m = 0; m < D; ++m) {
@@ -162,7 +172,60 @@ __device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
                 if (STAR && m != R && dx != 0) continue;
-                const int c = 2 * q + dx;  // first source column of the pair
+                const int c = q + dx;
+                if (c != 0 && c != 1) continue;
+                const float2 src = c == 0 ? P0 : P1;
+                if (first) {
+                    acc[slot][q] = fmul2(wgt2<R>(p, m, dx), src);
+                    first = false;
+                } else {
+                    acc[slot][q] = ffma2(wgt2<R>(p, m, dx), src, acc[slot][q]);
+                }
+            }
+        }
+    }
+}
+
+// Products whose source pair straddles a neighbour column.  col(j) is column
+// j of the extended row, j in [-R, 4+R): left halo, own, right halo.
+template <int R, bool STAR, class WS, class COL>
+__device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R + 1][2], const COL& col,
+                                              int j) {
+    constexpr int D = 2 * R + 1;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        if (STAR && m != R) continue;
+        const int slot = (j - m + R + 2 * D) % D;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                const int c = q + dx;
+                if (c == 0 || c == 1) continue;
+                acc[slot][q] = ffma2(wgt2<R>(p, m, dx), col.pair(c), acc[slot][q]);
+            }
+        }
+    }
+}
+
+// Adjacent pairing (used for R >= 2, where it measures faster): pairs
+// (c0, c1), (c2, c3), outputs (o0, o1), (o2, o3); the source of weight
+// (dy, dx) for pair q is (c[2q+dx], c[2q+dx+1]).  cur2 = {(c0,c1), (c2,c3)},
+// mid = (c1, c2); ext[i] = column i - R.
+template <int R, bool STAR, class WS>
+__device__ __forceinline__ void own_products_adj(const WS& p, float2 (&acc)[2 * R + 1][2],
+                                                 const float2 (&cur2)[2], float2 mid, int j) {
+    constexpr int D = 2 * R + 1;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        const int slot = (j - m + R + 2 * D) % D;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            bool first = (m == 0);
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                if (STAR && m != R && dx != 0) continue;
+                const int c = 2 * q + dx;
                 if (c < 0 || c + 1 > 3) continue;
                 const float2 src = (c == 0) ? cur2[0] : (c == 2 ? cur2[1] : mid);
                 if (first) {
@@ -176,11 +239,9 @@ __device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 
     }
 }
 
-// Products whose pair touches a neighbour column.  ext[i] = column i - R for
-// i in [0, 4 + 2R): left halo values, own values, right halo values.
 template <int R, bool STAR, class WS>
-__device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R + 1][2],
-                                              const float (&ext)[4 + 2 * R], int j) {
+__device__ __forceinline__ void halo_products_adj(const WS& p, float2 (&acc)[2 * R + 1][2],
+                                                  const float (&ext)[4 + 2 * R], int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
     for (int m = 0; m < D; ++m) {
@@ -198,6 +259,25 @@ __device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R +
         }
     }
 }
+
+// The extended row of one level-row for R = 1: own pairs plus the
+// neighbours' edge columns hl (column -1) and hr (column 4).
+template <int R>
+struct ExtRow {
+    float2 P0, P1;
+    float hl, hr;
+    __device__ __forceinline__ float at(int j) const {
+        switch (j) {
+            case 0: return P0.x;
+            case 1: return P1.x;
+            case 2: return P0.y;
+            case 3: return P1.y;
+        }
+        return j < 0 ? hl : hr;
+    }
+    // (column c, column c+2)
+    __device__ __forceinline__ float2 pair(int c) const { return make_float2(at(c), at(c + 2)); }
+};
 
 // One CTA's tile.  EDGE = the tile loads rows or columns outside the grid:
 // loads are bounds-checked (zero rule) or wrapped (periodic), and with the
@@ -220,12 +300,8 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
     const bool mask = EDGE && !periodic;
 
     bool col_in[4];
-    bool any_out = false;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        col_in[e] = !mask || (c0 + e >= 0 && c0 + e < nx);
-        any_out |= !col_in[e];
-    }
+    for (int e = 0; e < 4; ++e) col_in[e] = !mask || (c0 + e >= 0 && c0 + e < nx);
     const bool store_chunk = active && c0 >= x0 && c0 + 4 <= x0 + p.bx && c0 < nx;
 
     float2 acc[K][D][2];
@@ -289,50 +365,75 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                 if (s + 2 < nsteps) load_chunk_scalar<TS>(p, ybeg + s + 2, c0, active, nreg1);
             }
             float* bpar = ebuf + (s & 1) * SZ;
+            if constexpr (R == 1) {
+                // (c0, c2) / (c1, c3) pairs; edges through two scalar arrays.
+                float2 P0 = make_float2(cur[0], cur[2]), P1 = make_float2(cur[1], cur[3]);
 #pragma unroll
-            for (int l = 0; l < K; ++l) {
-                // Level l's row ybeg - l*R + s arrives; it feeds level l+1.
-                float* B = bpar + 2 * l * SZ;
-                if constexpr (R == 1) {
-                    B[tid + 1] = cur[0];
-                    B[kStreamMaxThreads + 2 + tid + 1] = cur[3];
-                } else {
-                    reinterpret_cast<float4*>(B)[tid + 1] = make_float4(cur[0], cur[1], cur[2], cur[3]);
+                for (int l = 0; l < K; ++l) {
+                    // Level l's row ybeg - l*R + s arrives; it feeds level l+1.
+                    float* B = bpar + 2 * l * SZ;
+                    B[tid + 1] = P0.x;                          // column 0
+                    B[kStreamMaxThreads + 2 + tid + 1] = P1.y;  // column 3
+                    own_products<R, STAR>(ws, acc[l], P0, P1, j);
+                    __syncthreads();
+                    ExtRow<R> ext;
+                    ext.P0 = P0;
+                    ext.P1 = P1;
+                    ext.hl = B[kStreamMaxThreads + 2 + tid];
+                    ext.hr = B[tid + 2];
+                    halo_products<R, STAR>(ws, acc[l], ext, j);
+                    // Output row (arriving row) - R of level l+1 is complete.
+                    const int cs = (j + R + 1) % D;
+                    P0 = acc[l][cs][0];
+                    P1 = acc[l][cs][1];
+                    if constexpr (EDGE) {
+                        if (mask) {
+                            const int yo = ybeg - (l + 1) * R + s;
+                            const bool row_out = yo < 0 || yo >= ny;
+                            if (row_out || !col_in[0]) P0.x = 0.f;
+                            if (row_out || !col_in[2]) P0.y = 0.f;
+                            if (row_out || !col_in[1]) P1.x = 0.f;
+                            if (row_out || !col_in[3]) P1.y = 0.f;
+                        }
+                    }
                 }
-                const float2 cur2[2] = {make_float2(cur[0], cur[1]), make_float2(cur[2], cur[3])};
-                own_products<R, STAR>(ws, acc[l], cur2, make_float2(cur[1], cur[2]), j);
-                __syncthreads();
-                float ext[4 + 2 * R];
+                cur[0] = P0.x;
+                cur[1] = P1.x;
+                cur[2] = P0.y;
+                cur[3] = P1.y;
+            } else {
+                // (c0, c1) / (c2, c3) pairs; edges through the whole 16-byte chunk.
 #pragma unroll
-                for (int e = 0; e < 4; ++e) ext[R + e] = cur[e];
-                if constexpr (R == 1) {
-                    ext[0] = B[kStreamMaxThreads + 2 + tid];
-                    ext[5] = B[tid + 2];
-                } else {
-                    float4 a = reinterpret_cast<const float4*>(B)[tid];
-                    float4 b = reinterpret_cast<const float4*>(B)[tid + 2];
+                for (int l = 0; l < K; ++l) {
+                    float* B = bpar + 2 * l * SZ;
+                    reinterpret_cast<float4*>(B)[tid + 1] = make_float4(cur[0], cur[1], cur[2], cur[3]);
+                    const float2 cur2[2] = {make_float2(cur[0], cur[1]), make_float2(cur[2], cur[3])};
+                    own_products_adj<R, STAR>(ws, acc[l], cur2, make_float2(cur[1], cur[2]), j);
+                    __syncthreads();
+                    float ext[4 + 2 * R];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) ext[R + e] = cur[e];
+                    const float4 a = reinterpret_cast<const float4*>(B)[tid];
+                    const float4 b = reinterpret_cast<const float4*>(B)[tid + 2];
                     const float lft[4] = {a.x, a.y, a.z, a.w}, rgt[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                     for (int i = 0; i < R; ++i) {
                         ext[i] = lft[4 - R + i];
                         ext[R + 4 + i] = rgt[i];
                     }
-                }
-                halo_products<R, STAR>(ws, acc[l], ext, j);
-                // Output row (arriving row) - R of level l+1 is complete.
-                const int cs = (j + R + 1) % D;
-                cur[0] = acc[l][cs][0].x; cur[1] = acc[l][cs][0].y;
-                cur[2] = acc[l][cs][1].x; cur[3] = acc[l][cs][1].y;
-                if constexpr (EDGE) {
-                    if (mask) {
-                        const int yo = ybeg - (l + 1) * R + s;
-                        if (yo < 0 || yo >= ny) {
+                    halo_products_adj<R, STAR>(ws, acc[l], ext, j);
+                    const int cs = (j + R + 1) % D;
+                    cur[0] = acc[l][cs][0].x;
+                    cur[1] = acc[l][cs][0].y;
+                    cur[2] = acc[l][cs][1].x;
+                    cur[3] = acc[l][cs][1].y;
+                    if constexpr (EDGE) {
+                        if (mask) {
+                            const int yo = ybeg - (l + 1) * R + s;
+                            const bool row_out = yo < 0 || yo >= ny;
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) cur[e] = 0.f;
-                        }
-                        if (any_out) {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) cur[e] = col_in[e] ? cur[e] : 0.f;
+                            for (int e = 0; e < 4; ++e)
+                                if (row_out || !col_in[e]) cur[e] = 0.f;
                         }
                     }
                 }
