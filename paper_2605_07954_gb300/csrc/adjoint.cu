@@ -15,7 +15,7 @@
 // paths use the same per-point arithmetic, so the result does not depend on s.
 //
 // adjoint_step_kernel fuses, for one step, the lambda update and the
-// weight-gradient products: a CTA stages a 32x32 tile of lambda_{t+1} and of
+// weight-gradient products: a CTA stages a 32x64 tile of lambda_{t+1} and of
 // u_t with an R-wide halo in shared memory, writes lambda_t for the tile, and
 // adds the tile's (2R+1)^2 products lambda_{t+1} * shifted(u_t) to a per-tile
 // FP64 partial.  Tile t of a launch is always CTA t and launches are ordered,
@@ -38,67 +38,122 @@ void plan_weights(const stencil_plan_t* p, float* w);
 void** plan_aux(stencil_plan_t* p, void (**freer)(void*));
 void plan_set_aux_free(stencil_plan_t* p, void (*freer)(void*));
 
-constexpr int kAdjTile = 32;  // output tile side
-constexpr int kAdjRowsPerThread = 4;
+constexpr int kAdjTX = 32;          // output tile columns (one per lane)
+constexpr int kAdjTY = 64;          // output tile rows
+constexpr int kAdjRowsPerThread = 8;  // 8 warps x 8 rows
 
+// One reverse step on a 32 x 64 tile.  Lane tx owns column x0 + tx and warp ty
+// rows y0 + 8 ty .. + 7; it walks its rows keeping the last 2R+1 staged rows
+// of lambda_{t+1} and u_t (its column +- R) in registers, so each row costs
+// 2 (2R+1) shared-memory loads for (2R+1)^2 lambda FMAs and (2R+1)^2 gradient FMAs.
 template <int R>
 __global__ void __launch_bounds__(256)
     adjoint_step_kernel(const float* __restrict__ lam_in, const float* __restrict__ u,
                         float* __restrict__ lam_out, double* __restrict__ partials, int ny, int nx,
                         int periodic, Weights w, int tiles_x) {
     constexpr int D = 2 * R + 1;
-    constexpr int S = kAdjTile + 2 * R;  // staged side
-    __shared__ float sl[S][S + 1];
-    __shared__ float su[S][S + 1];
+    constexpr int SY = kAdjTY + 2 * R, SX = kAdjTX + 2 * R;
+    __shared__ float sl[SY][SX + 1];
+    __shared__ float su[SY][SX + 1];
     __shared__ float red[8][D * D];
     const int tx = threadIdx.x, ty = threadIdx.y;  // (32, 8)
-    const int tid = ty * 32 + tx;
-    const int x0 = (blockIdx.x % tiles_x) * kAdjTile;
-    const int y0 = (blockIdx.x / tiles_x) * kAdjTile;
+    const int x0 = (blockIdx.x % tiles_x) * kAdjTX;
+    const int y0 = (blockIdx.x / tiles_x) * kAdjTY;
 
-    // Stage both tiles with their halo (zero outside, or wrapped).
-    for (int i = tid; i < S * S; i += 256) {
-        const int r = i / S, c = i % S;
-        int y = y0 - R + r, x = x0 - R + c;
-        float a = 0.f, b = 0.f;
-        if (periodic) {
-            y = (y % ny + ny) % ny;
-            x = (x % nx + nx) % nx;
-            a = lam_in[(size_t)y * nx + x];
-            b = u[(size_t)y * nx + x];
-        } else if (y >= 0 && y < ny && x >= 0 && x < nx) {
-            a = lam_in[(size_t)y * nx + x];
-            b = u[(size_t)y * nx + x];
+    // Stage both tiles with their halo (zero outside, or wrapped).  Every
+    // thread issues all of its loads before its first shared-memory store, so
+    // the DRAM latencies overlap.  Item i = tid + 256 it is staged row i / SX,
+    // column i % SX, advanced without division.
+    {
+        constexpr int ITEMS = SY * SX, ITERS = (ITEMS + 255) / 256;
+        const int tid0 = ty * 32 + tx;
+        int r = tid0 / SX, c = tid0 % SX;
+        float va[ITERS], vb[ITERS];
+        int ra[ITERS], ca[ITERS];
+#pragma unroll
+        for (int it = 0; it < ITERS; ++it) {
+            ra[it] = r;
+            ca[it] = c;
+            va[it] = vb[it] = 0.f;
+            if (r < SY) {
+                int y = y0 - R + r, x = x0 - R + c;
+                bool ok = y >= 0 && y < ny && x >= 0 && x < nx;
+                if (periodic) {
+                    y = (y % ny + ny) % ny;
+                    x = (x % nx + nx) % nx;
+                    ok = true;
+                }
+                if (ok) {
+                    const size_t i = (size_t)y * nx + x;
+                    va[it] = __ldg(lam_in + i);
+                    vb[it] = __ldg(u + i);
+                }
+            }
+            c += 256 % SX;
+            r += 256 / SX;
+            if (c >= SX) {
+                c -= SX;
+                ++r;
+            }
         }
-        sl[r][c] = a;
-        su[r][c] = b;
+#pragma unroll
+        for (int it = 0; it < ITERS; ++it) {
+            if (ra[it] < SY) {
+                sl[ra[it]][ca[it]] = va[it];
+                su[ra[it]][ca[it]] = vb[it];
+            }
+        }
     }
     __syncthreads();
 
     float g[D * D];
 #pragma unroll
     for (int k = 0; k < D * D; ++k) g[k] = 0.f;
+    // Register windows: wl[i][e] = lambda staged row (row0 + i), column tx + e;
+    // wu likewise for u.  The output row o = r0 + k needs lambda rows o-R..o+R
+    // (flipped correlation) and u rows o-R..o+R.
+    const int r0 = ty * kAdjRowsPerThread;  // first output row (tile-local)
+    float wl[D][D], wu[D][D];
 #pragma unroll
-    for (int rr = 0; rr < kAdjRowsPerThread; ++rr) {
-        const int ly = ty + 8 * rr, lx = tx;
-        const int y = y0 + ly, x = x0 + lx;
+    for (int i = 0; i < D - 1; ++i)
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            wl[i + 1][e] = sl[r0 + i][tx + e];
+            wu[i + 1][e] = su[r0 + i][tx + e];
+        }
+#pragma unroll
+    for (int k = 0; k < kAdjRowsPerThread; ++k) {
+        // slide: drop the oldest staged row, append staged row r0 + k + 2R
+#pragma unroll
+        for (int i = 0; i < D - 1; ++i)
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                wl[i][e] = wl[i + 1][e];
+                wu[i][e] = wu[i + 1][e];
+            }
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            wl[D - 1][e] = sl[r0 + k + 2 * R][tx + e];
+            wu[D - 1][e] = su[r0 + k + 2 * R][tx + e];
+        }
+        // window row i holds staged row r0 + k + i, i.e. grid row o - R + i for o = y0 + r0 + k
+        const int y = y0 + r0 + k, x = x0 + tx;
         if (y >= ny || x >= nx) continue;
-        // lambda_t[p] = sum_d W[d] lambda_{t+1}[p - d], dy-major then dx
+        // lambda_t[o] = sum_d W[d] lambda_{t+1}[o - d], dy-major then dx
         float acc = 0.f;
 #pragma unroll
         for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx)
-                acc = fmaf(w.w[(dy + R) * D + (dx + R)], sl[ly + R - dy][lx + R - dx], acc);
+                acc = fmaf(w.w[(dy + R) * D + (dx + R)], wl[R - dy][R - dx], acc);
         lam_out[(size_t)y * nx + x] = acc;
-        // dL/dW[d] += lambda_{t+1}[p] * u_t[p + d]
-        const float lp = sl[ly + R][lx + R];
+        // dL/dW[d] += lambda_{t+1}[o] * u_t[o + d]
+        const float lp = wl[R][R];
 #pragma unroll
         for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx)
-                g[(dy + R) * D + (dx + R)] =
-                    fmaf(lp, su[ly + R + dy][lx + R + dx], g[(dy + R) * D + (dx + R)]);
+                g[(dy + R) * D + (dx + R)] = fmaf(lp, wu[R + dy][R + dx], g[(dy + R) * D + (dx + R)]);
     }
     // Fixed-order reduction: butterfly within each warp, then warps in order.
 #pragma unroll
@@ -109,6 +164,7 @@ __global__ void __launch_bounds__(256)
         if (tx == 0) red[ty][k] = v;
     }
     __syncthreads();
+    const int tid = ty * 32 + tx;
     if (tid < D * D) {
         double s = 0.0;
         for (int wv = 0; wv < 8; ++wv) s += (double)red[wv][tid];
@@ -116,14 +172,23 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// grad_w[k] = sum over tiles of partials[tile][k], tiles in increasing order.
-__global__ void reduce_partials_kernel(const double* __restrict__ partials, int tiles, int taps,
-                                       double* __restrict__ grad_w) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= taps) return;
+// grad_w[k] = sum over tiles of partials[tile][k] in a fixed order: thread i of
+// the block sums tiles i, i + 256, ... in increasing order, then the 256
+// thread sums are added pairwise in a fixed tree.  One block per tap.
+__global__ void __launch_bounds__(256)
+    reduce_partials_kernel(const double* __restrict__ partials, int tiles, int taps,
+                           double* __restrict__ grad_w) {
+    __shared__ double sh[256];
+    const int k = blockIdx.x;
     double s = 0.0;
-    for (int t = 0; t < tiles; ++t) s += partials[(size_t)t * taps + k];
-    grad_w[k] = s;
+    for (int t = threadIdx.x; t < tiles; t += 256) s += partials[(size_t)t * taps + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grad_w[k] = sh[0];
 }
 
 static const void* adjoint_kernel(int R) {
@@ -232,8 +297,8 @@ stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const voi
     plan_weights(plan, wf.w);
     Weights wadj = wf;  // the step kernel indexes W directly; flip is in its loop
 
-    const int tiles_x = (nx + kAdjTile - 1) / kAdjTile;
-    const int tiles = tiles_x * ((ny + kAdjTile - 1) / kAdjTile);
+    const int tiles_x = (nx + kAdjTX - 1) / kAdjTX;
+    const int tiles = tiles_x * ((ny + kAdjTY - 1) / kAdjTY);
     if (T == 0) {
         if (grad_u0 != grad_uT) ACK(cudaMemcpyAsync(grad_u0, grad_uT, bytes, cudaMemcpyDeviceToDevice, st));
         if (grad_w) ACK(cudaMemsetAsync(grad_w, 0, sizeof(double) * D * D, st));
@@ -287,7 +352,7 @@ stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const voi
     ACK(cudaMemcpyAsync(grad_u0, lam[cur], bytes, cudaMemcpyDeviceToDevice, st));
     if (grad_w) {
         const int taps = D * D;
-        reduce_partials_kernel<<<1, 64, 0, st>>>(partials, tiles, taps, grad_w);
+        reduce_partials_kernel<<<taps, 256, 0, st>>>(partials, tiles, taps, grad_w);
         ACK(cudaGetLastError());
     }
     return STENCIL_OK;
