@@ -158,6 +158,24 @@ int64_t stencil_run_launches(const stencil_plan_t* plan, int64_t T);
 stencil_status_t stencil_plan_status(stencil_plan_t* plan);
 
 /*
+ * T steps with a convergence check every m steps (the paper's periodic
+ * convergence checks, Sec. IV).  After every m-th step t (t = m, 2m, ... <= T)
+ * residuals[t/m - 1] = || u_t - u_{t-1} ||_2 over the whole grid (FP64,
+ * deterministic).  Same operation, arguments and result bits as stencil_run
+ * (periodic grids with nx % 4 != 0: the same values up to rounding, since
+ * their results depend on the launch depths at the rounding level).
+ *   residuals  DEVICE, floor(T/m) doubles, written.
+ *   m          >= 1.
+ * Each checked interval runs m-1 steps temporally blocked and its last step
+ * as a single launch into a second buffer (the plan keeps two extra grids).
+ */
+stencil_status_t stencil_run_residual(stencil_plan_t* plan, const void* in, void* out, int64_t T,
+                                      int64_t m, double* residuals, stencil_stream_t stream);
+
+/* Message for the last failure of stencil_run_residual on the calling thread. */
+const char* stencil_residual_last_error(void);
+
+/*
  * Reverse-mode gradient of T steps (the adjoint of the Sec. II-C update).
  * For a loss L(u_T) whose gradient at u_T is grad_uT:
  *     lambda_T = grad_uT,  lambda_t = A^T lambda_{t+1}  (correlation with the

@@ -97,6 +97,19 @@ class Plan:
                                        _current_stream_handle()), "stencil_run")
         return out
 
+    def run_residual(self, x, T: int, m: int, out=None):
+        """u_T and the residuals ||u_t - u_{t-1}||_2 after every m-th step (CUDA float64)."""
+        torch = self._check_tensor(x)
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            self._check_tensor(out)
+        res = torch.empty(max(1, int(T) // int(m)), dtype=torch.float64, device=x.device)
+        check(_capi.load().stencil_run_residual(self._h, x.data_ptr(), out.data_ptr(), int(T), int(m),
+                                                res.data_ptr(), _current_stream_handle()),
+              "stencil_run_residual")
+        return out, res[: int(T) // int(m)]
+
     def run_host(self, x: np.ndarray, T: int, out: np.ndarray | None = None, stream: int = 0):
         """Host in, host out: H2D copy, T steps and D2H copy, synchronised."""
         if x.shape != self.shape or not x.flags["C_CONTIGUOUS"]:

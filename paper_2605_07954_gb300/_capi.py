@@ -74,6 +74,8 @@ _PROTOS = {
     "stencil_status_string": (ctypes.c_char_p, [_i32]),
     "stencil_last_error": (ctypes.c_char_p, []),
     "stencil_version": (_i32, []),
+    "stencil_run_residual": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _vp]),
+    "stencil_residual_last_error": (ctypes.c_char_p, []),
     "stencil_adjoint": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp]),
     "stencil_adjoint_launches": (_i64, [_vp, _i64, _i64]),
     "stencil_adjoint_last_error": (ctypes.c_char_p, []),
@@ -123,7 +125,9 @@ class StencilError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib = load()
         name = lib.stencil_status_string(status).decode()
-        if "adjoint" in where:
+        if "residual" in where:
+            msg = lib.stencil_residual_last_error().decode()
+        elif "adjoint" in where:
             msg = lib.stencil_adjoint_last_error().decode()
         elif "batch" in where:
             msg = lib.stencil_batch_last_error().decode()

@@ -35,8 +35,8 @@ namespace gbst {
 
 // Internal accessors of a plan (plan.cu).
 void plan_weights(const stencil_plan_t* p, float* w);
-void** plan_aux(stencil_plan_t* p, void (**freer)(void*));
-void plan_set_aux_free(stencil_plan_t* p, void (*freer)(void*));
+void** plan_aux_slot(stencil_plan_t* p, int id);
+void plan_set_aux_free(stencil_plan_t* p, int id, void (*freer)(void*));
 
 constexpr int kAdjTX = 32;          // output tile columns (one per lane)
 constexpr int kAdjTY = 64;          // output tile rows
@@ -237,14 +237,13 @@ void adj_scratch_free(void* v) {
 
 stencil_status_t adj_scratch(stencil_plan_t* plan, size_t grids, size_t grid_bytes, size_t npartials,
                              AdjScratch** out) {
-    void (*freer)(void*) = nullptr;
-    void** slot = plan_aux(plan, &freer);
+    void** slot = plan_aux_slot(plan, 0);
     AdjScratch* sc = static_cast<AdjScratch*>(*slot);
     if (!sc) {
         sc = new (std::nothrow) AdjScratch();
         if (!sc) return afail(STENCIL_ERR_OOM, "host allocation failed");
         *slot = sc;
-        plan_set_aux_free(plan, adj_scratch_free);
+        plan_set_aux_free(plan, 0, adj_scratch_free);
     }
     if (sc->grids < grids) {
         if (sc->base) cudaFree(sc->base);

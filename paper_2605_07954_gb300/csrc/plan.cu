@@ -88,20 +88,17 @@ struct stencil_plan {
     void* host_out = nullptr;
     unsigned int* status = nullptr;
     cudaStream_t last_stream = nullptr;
-    // Scratch of another subsystem (the adjoint), released with the plan.
-    void* aux = nullptr;
-    void (*aux_free)(void*) = nullptr;
+    // Scratch of other subsystems (0: adjoint, 1: residual runs), released with the plan.
+    void* aux[4] = {nullptr, nullptr, nullptr, nullptr};
+    void (*aux_free[4])(void*) = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace gbst {
 void plan_weights(const stencil_plan_t* p, float* w) {
     for (int i = 0; i < kMaxTaps; ++i) w[i] = p->w.w[i];
 }
-void** plan_aux(stencil_plan_t* p, void (**freer)(void*)) {
-    *freer = p->aux_free;
-    return &p->aux;
-}
-void plan_set_aux_free(stencil_plan_t* p, void (*freer)(void*)) { p->aux_free = freer; }
+void** plan_aux_slot(stencil_plan_t* p, int id) { return &p->aux[id]; }
+void plan_set_aux_free(stencil_plan_t* p, int id, void (*freer)(void*)) { p->aux_free[id] = freer; }
 }  // namespace gbst
 
 static size_t elem_size(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
@@ -518,7 +515,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
 
 void stencil_plan_destroy(stencil_plan_t* p) {
     if (!p) return;
-    if (p->aux && p->aux_free) p->aux_free(p->aux);
+    for (int i = 0; i < 4; ++i)
+        if (p->aux[i] && p->aux_free[i]) p->aux_free[i](p->aux[i]);
     if (p->ws) cudaFree(p->ws);
     if (p->host_in) cudaFree(p->host_in);
     if (p->host_out) cudaFree(p->host_out);

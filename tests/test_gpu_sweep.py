@@ -311,3 +311,43 @@ def test_autotune_first_run(oracle, name):
     assert rel_l2(y.cpu().numpy(), ref) <= fp32_tol(40)
     assert torch.equal(x, torch.from_numpy(u0).cuda())
     p.close()
+
+
+@pytest.mark.parametrize("name", PATTERNS)
+@pytest.mark.parametrize("boundary,shape", [("zero", (130, 257)), ("zero", (96, 256)),
+                                            ("periodic", (96, 256)), ("periodic", (131, 260))])
+def test_depth_does_not_change_bits(name, boundary, shape):
+    """Every step is the same per-point arithmetic whatever the temporal-blocking
+    depth or tiling, so all depths give the same bits.  (Periodic grids whose
+    width is not a multiple of 4 are the exception: a wrapped column's image sits
+    at another position of a thread's 4-column chunk and is summed in another
+    order, so results there agree only to rounding; see test_periodic_unaligned_depths.)"""
+    from paper_2605_07954_gb300 import Plan
+    shp, r = inputs.PATTERNS[name]
+    W = inputs.pattern_weights(name)
+    x = torch.from_numpy(inputs.field(*shape)).cuda()
+    outs = {}
+    for k in DEPTHS[(r, shp)]:
+        p = Plan(shape[0], shape[1], W, boundary=boundary, tb_depth=k)
+        outs[k] = p.run(x, 12)
+        torch.cuda.synchronize()
+        p.close()
+    ks = sorted(outs)
+    bad = [k for k in ks if not torch.equal(outs[k], outs[ks[0]])]
+    assert not bad, (name, boundary, shape, bad)
+
+
+@pytest.mark.parametrize("name", PATTERNS)
+def test_periodic_unaligned_depths(oracle, name):
+    """Periodic, width not a multiple of 4: every depth matches the oracle."""
+    from paper_2605_07954_gb300 import Plan
+    shp, r = inputs.PATTERNS[name]
+    W = inputs.pattern_weights(name)
+    u0 = inputs.field(130, 257)
+    ref = oracle.sweep_f64(u0, W, 12, "periodic")
+    x = torch.from_numpy(u0).cuda()
+    for k in DEPTHS[(r, shp)]:
+        p = Plan(130, 257, W, boundary="periodic", tb_depth=k)
+        got = p.run(x, 12).cpu().numpy()
+        p.close()
+        assert rel_linf(got, ref) <= fp32_elem_tol(12, _taps(W)), k
