@@ -72,12 +72,20 @@ typedef enum {
     STENCIL_COMPUTE_TC_BF16 = 3
 } stencil_compute_t;
 
-/* Kernel family for the CUDA-core engine. */
+/* Kernel family.  The tensor-core contraction (7x7 box, one step per launch)
+ * has two engines: warp-level MMAs (any storage/engine pair, both boundaries)
+ * and tcgen05 MMAs with tensor-memory accumulators and TMA-staged operands,
+ * which take zero-boundary grids stored in the MMA operand type (BF16 storage
+ * with TC_BF16, FP32 with TC_TF32), rows of a multiple of 16 bytes,
+ * ny >= 134 and nx >= 128.  With TC_TF32 the first launch of a run (which rounds the
+ * caller's FP32 input to TF32) always runs on the warp-MMA engine. */
 typedef enum {
     STENCIL_KERNEL_AUTO = 0,
     STENCIL_KERNEL_NAIVE = 1,      /* one thread per point, one step per launch      */
     STENCIL_KERNEL_STREAM = 2,     /* row-streaming tiles, k steps per launch        */
-    STENCIL_KERNEL_TC = 3          /* tensor-core contraction (7x7 box), 1 step/launch */
+    STENCIL_KERNEL_TC = 3,         /* tensor cores: tcgen05 where it applies, else warp MMA */
+    STENCIL_KERNEL_TC_WARP = 4,    /* tensor cores, warp-MMA engine only             */
+    STENCIL_KERNEL_TC_UMMA = 5     /* tensor cores, tcgen05 engine (UNSUPPORTED where it does not apply) */
 } stencil_kernel_t;
 
 /* Optional plan settings; pass NULL for defaults.  0 means "choose". */
@@ -88,6 +96,7 @@ typedef struct {
     int threads;      /* threads per CTA of the streaming kernel (multiple of 32)   */
     int tile_rows;    /* output rows per CTA tile of the streaming kernel           */
     int autotune;     /* 1: time candidate configurations on first run              */
+    int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16/32)   */
 } stencil_options_t;
 
 /* What a plan decided.  Filled by stencil_plan_info(). */
@@ -104,6 +113,7 @@ typedef struct {
     int ctas;              /* CTAs per launch                                       */
     int smem_bytes;        /* dynamic shared memory per CTA                         */
     int64_t workspace_bytes;  /* device workspace the plan owns                    */
+    int mma_n;             /* tcgen05 engine in use: N of one MMA; 0 = not in use   */
 } stencil_plan_info_t;
 
 typedef struct stencil_plan stencil_plan_t;

@@ -18,7 +18,7 @@ from ._capi import StencilError, check
 DTYPES = {"f32": _capi.STENCIL_F32, "bf16": _capi.STENCIL_BF16, "f16": _capi.STENCIL_F16}
 BOUNDARIES = {"zero": _capi.STENCIL_BOUNDARY_ZERO, "periodic": _capi.STENCIL_BOUNDARY_PERIODIC}
 COMPUTES = {"auto": 0, "fp32": 1, "tc_tf32": 2, "tc_bf16": 3}
-KERNELS = {"auto": 0, "naive": 1, "stream": 2}
+KERNELS = {"auto": 0, "naive": 1, "stream": 2, "tc": 3, "tc_warp": 4, "tc_umma": 5}
 
 
 def _torch_dtype_name(t) -> str:
@@ -36,7 +36,7 @@ class Plan:
 
     def __init__(self, ny: int, nx: int, weights, dtype: str = "f32", boundary: str = "zero",
                  compute: str = "auto", kernel: str = "auto", tb_depth: int = 0,
-                 threads: int = 0, tile_rows: int = 0, autotune: bool = False):
+                 threads: int = 0, tile_rows: int = 0, autotune: bool = False, mma_n: int = 0):
         lib = _capi.load()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
         d = w.shape[0]
@@ -47,7 +47,7 @@ class Plan:
         self.dtype = dtype
         self.weights = w
         opt = _capi.stencil_options_t(COMPUTES[compute], KERNELS[kernel], int(tb_depth),
-                                      int(threads), int(tile_rows), int(bool(autotune)))
+                                      int(threads), int(tile_rows), int(bool(autotune)), int(mma_n))
         h = ctypes.c_void_p()
         check(lib.stencil_plan_create(ctypes.byref(h), int(ny), int(nx), self.radius,
                                       w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),

@@ -28,7 +28,8 @@ STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_STREAM = 0, 1, 2
 
 class stencil_options_t(ctypes.Structure):
     _fields_ = [("compute", ctypes.c_int), ("kernel", ctypes.c_int), ("tb_depth", ctypes.c_int),
-                ("threads", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("mma_n", ctypes.c_int)]
 
 
 class stencil_plan_info_t(ctypes.Structure):
@@ -37,7 +38,7 @@ class stencil_plan_info_t(ctypes.Structure):
                 ("compute", ctypes.c_int), ("kernel", ctypes.c_int), ("tb_depth", ctypes.c_int),
                 ("threads", ctypes.c_int), ("halo_cols", ctypes.c_int), ("tile_cols", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("ctas", ctypes.c_int), ("smem_bytes", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_int64), ("mma_n", ctypes.c_int)]
 
 
 class stencil_grid_desc_t(ctypes.Structure):

@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(256) box49_tc_kernel(const __grid_constant__ T
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
     tile_mma<BF16MMA>(BF16MMA ? (const void*)s16 : (const void*)s32, warp, lane, bfr, acc);
-    store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, false);
+    // FP32 storage, TF32 engine: intermediate states stay TF32-rounded, as
+    // the pipelined and tcgen05 engines expect (rounding at load is idempotent).
+    store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, !BF16MMA && sizeof(TS) == 4 && p.round_out);
 }
 
 // ---- persistent, double-buffered (16-byte aligned rows) ---------------------------

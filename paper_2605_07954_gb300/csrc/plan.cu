@@ -34,6 +34,11 @@ const void* get_naive_kernel(int radius, int dtype);
 const void* get_box49_tc_kernel(int dtype, int bf16mma);
 const void* get_box49_tc_pipe_kernel(int dtype, int bf16mma);
 int box49_tc_smem_bytes(int bf16mma);
+const void* get_box49_umma_kernel(int tf32, int nt);
+int box49_umma_smem_bytes(int tf32, int nt);
+int box49_umma_threads();
+cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int ny, int nx, int ld,
+                              int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st);
 struct TcParams {  // must match box49_tc.cu
     const void* in;
     void* out;
@@ -78,6 +83,9 @@ struct stencil_plan {
     int per_sm = 0;
     const void* tc_pipe = nullptr;  // persistent double-buffered tensor-core kernel
     int tc_pipe_smem = 0, tc_pipe_ctas = 0;
+    int umma_n = 0;     // tcgen05 engine in use: N of one MMA (0: warp-MMA engine)
+    int umma_ok = 0;    // usable tcgen05 MMA widths, bit n / 16
+    int umma_ctas = 0;
     unsigned smem_set = 0;  // bit 2k+vec: that kernel's shared-memory attribute is set
     int tuned = 0;
     const void* naive = nullptr;
@@ -206,6 +214,61 @@ static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, in
     return STENCIL_OK;
 }
 
+// Default N of one tcgen05 MMA per operand type (BF16, TF32), and whether
+// that engine is the default for the tensor-core kernel family (kernel = TC or
+// AUTO without autotuning).  Measured on GB300 at 16384^2: the tcgen05 engine
+// (687 / 352 GStencil/s, BF16 / TF32) does not yet beat the warp-MMA engine
+// (709 / 421), so the warp engine stays the default; autotuning times both.
+static const int kUmmaDefaultN[2] = {32, 16};
+static const int kUmmaPreferred[2] = {0, 0};
+
+// The tcgen05 engine (box49_umma.cu) takes zero-boundary grids whose storage is
+// the MMA operand type (BF16 storage for TC_BF16, FP32 for TC_TF32), with
+// 16-byte aligned rows and at least one full staged tile.  With TF32 the first
+// launch of a run stays on the warp-MMA engine, which rounds the caller's
+// input (and every output but the last) to TF32.  kernel = TC_UMMA makes the
+// engine mandatory, TC_WARP switches it off.  p->umma_ok collects the usable
+// MMA widths (bit n / 16), p->umma_n the one in use (0: warp-MMA engine).
+static stencil_status_t configure_umma(stencil_plan* p) {
+    p->umma_n = 0;
+    p->umma_ok = 0;
+    const int want = p->opt.kernel;
+    if (want == STENCIL_KERNEL_TC_WARP) return STENCIL_OK;
+    const int tf32 = p->compute == STENCIL_COMPUTE_TC_TF32;
+    const char* why = nullptr;
+    if (p->boundary != STENCIL_BOUNDARY_ZERO) why = "the tcgen05 engine takes zero-boundary grids";
+    else if (tf32 ? p->dtype != STENCIL_F32 : p->dtype != STENCIL_BF16)
+        why = "the tcgen05 engine needs FP32 storage for TF32 and BF16 storage for BF16";
+    else if ((p->nx * (int64_t)p->elem) % 16 != 0) why = "the tcgen05 engine needs rows of a multiple of 16 bytes";
+    else if (p->ny < 134 || p->nx < 128) why = "the tcgen05 engine needs ny >= 134 and nx >= 128";
+    else if (p->opt.mma_n > 0 && !get_box49_umma_kernel(tf32, p->opt.mma_n))
+        why = "no tcgen05 kernel for this mma_n (BF16: 16, 32, 64; TF32: 16, 32)";
+    if (!why) {
+        for (int nt = 16; nt <= 64; nt *= 2) {
+            if (p->opt.mma_n > 0 && nt != p->opt.mma_n) continue;
+            const void* fn = get_box49_umma_kernel(tf32, nt);
+            if (!fn) continue;
+            const int smem = box49_umma_smem_bytes(tf32, nt);
+            CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            int per_sm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, box49_umma_threads(), smem));
+            if (per_sm >= 1) p->umma_ok |= 1 << (nt / 16);
+        }
+        if (!p->umma_ok) why = "the tcgen05 kernel does not fit an SM";
+    }
+    if (why) {
+        if (want == STENCIL_KERNEL_TC_UMMA) return fail(STENCIL_ERR_UNSUPPORTED, why);
+        return STENCIL_OK;
+    }
+    // One CTA per SM: each holds 256 tensor-memory columns for its whole life.
+    p->umma_ctas = (int)std::min<int64_t>((int64_t)p->sms, (int64_t)p->strips * p->tiles_y);
+    const int nt = p->opt.mma_n > 0 ? p->opt.mma_n : kUmmaDefaultN[tf32];
+    if (want == STENCIL_KERNEL_TC_UMMA || kUmmaPreferred[tf32]) p->umma_n = (p->umma_ok >> (nt / 16)) & 1 ? nt : 0;
+    if (want == STENCIL_KERNEL_TC_UMMA && !p->umma_n) return fail(STENCIL_ERR_UNSUPPORTED, "tcgen05 kernel unusable");
+    p->kernel = p->umma_n ? STENCIL_KERNEL_TC_UMMA : STENCIL_KERNEL_TC;
+    return STENCIL_OK;
+}
+
 static stencil_status_t configure_tc(stencil_plan* p) {
     if (p->R != 3) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engines need radius 3 (7x7 weights)");
     if (p->dtype == STENCIL_F16) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engines take FP32 or BF16 storage");
@@ -234,7 +297,7 @@ static stencil_status_t configure_tc(stencil_plan* p) {
             p->tc_pipe_ctas = (int)std::min<int64_t>((int64_t)per_sm * p->sms, (int64_t)p->strips * p->tiles_y);
         }
     }
-    return STENCIL_OK;
+    return configure_umma(p);
 }
 
 static stencil_status_t configure_naive(stencil_plan* p) {
@@ -257,7 +320,7 @@ static stencil_status_t configure_naive(stencil_plan* p) {
 // the first launch and keeps intermediate states TF32-rounded until the last).
 static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst, int nlev,
                                     cudaStream_t st, int first = 1, int last = 1) {
-    if (p->kernel == STENCIL_KERNEL_TC) {
+    if (p->kernel == STENCIL_KERNEL_TC || p->kernel == STENCIL_KERNEL_TC_UMMA) {
         TcParams tp{};
         tp.in = src;
         tp.out = dst;
@@ -272,6 +335,14 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
         tp.convert_in = first;
         tp.round_out = !last;
         for (int i = 0; i < 49; ++i) tp.w[i] = p->w.w[i];
+        const int tf32 = p->compute == STENCIL_COMPUTE_TC_TF32;
+        if (p->umma_n && !(tf32 && first) && (uintptr_t)src % 16 == 0 && (uintptr_t)dst % 16 == 0) {
+            const cudaError_t e = launch_box49_umma(tf32, p->umma_n, src, dst, tp.ny, tp.nx, tp.ld,
+                                                    tf32 && !last, p->status, p->w.w, p->umma_ctas, st);
+            if (e == cudaSuccess) return STENCIL_OK;
+            if (e != cudaErrorNotSupported) CK(e);
+            // no tensor map for this layout: the warp-MMA engine takes the step
+        }
         void* args[] = {&tp};
         if (p->tc_pipe && tp.vec) {
             CK(cudaLaunchKernel(p->tc_pipe, dim3((unsigned)p->tc_pipe_ctas), dim3(256), args,
@@ -364,6 +435,56 @@ static stencil_status_t time_launch(stencil_plan* p, const void* in, int reps, c
     return STENCIL_OK;
 }
 
+// Tensor-core plans: time the warp-MMA engine and every usable tcgen05 MMA
+// width (one step per launch, `in` into the workspace) and keep the fastest.
+// A plan created with kernel = TC_UMMA, or with mma_n set, keeps that choice.
+typedef std::tuple<int64_t, int64_t, int, int, int> TcTuneKey;
+static std::map<TcTuneKey, int> g_tc_tune_cache;
+
+static stencil_status_t autotune_tc(stencil_plan* p, const void* in, cudaStream_t st) {
+    if (!p->umma_ok || p->opt.kernel == STENCIL_KERNEL_TC_UMMA || p->opt.mma_n > 0) return STENCIL_OK;
+    const TcTuneKey key(p->ny, p->nx, p->dtype, p->compute, p->device);
+    int best_n = -1;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tc_tune_cache.find(key);
+        if (it != g_tc_tune_cache.end()) best_n = it->second;
+    }
+    if (best_n < 0) {
+        const int reps = (int)std::max(2.0, std::min(32.0, 4e9 / ((double)p->ny * (double)p->nx)));
+        float best = 1e30f;
+        for (int nt = 0; nt <= 64; nt = nt ? 2 * nt : 16) {
+            if (nt && !((p->umma_ok >> (nt / 16)) & 1)) continue;
+            p->umma_n = nt;
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            stencil_status_t s = launch_once(p, in, p->ws, 1, st, 0, 1);  // warm-up
+            if (s == STENCIL_OK) {
+                cudaEventRecord(e0, st);
+                for (int i = 0; i < reps && s == STENCIL_OK; ++i) s = launch_once(p, in, p->ws, 1, st, 0, 1);
+                cudaEventRecord(e1, st);
+            }
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (s == STENCIL_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (s != STENCIL_OK) return s;
+            if (e != cudaSuccess) return fail(STENCIL_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+            if (ms < best) {
+                best = ms;
+                best_n = nt;
+            }
+        }
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tc_tune_cache[key] = best_n;
+    }
+    p->umma_n = best_n;
+    p->kernel = best_n ? STENCIL_KERNEL_TC_UMMA : STENCIL_KERNEL_TC;
+    return STENCIL_OK;
+}
+
 static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t st) {
     const TuneKey key(p->ny, p->nx, p->R, p->star, p->dtype, p->boundary, p->device);
     {
@@ -438,7 +559,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     stencil_options_t o{};
     if (opt) o = *opt;
     if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_BF16 || o.kernel < 0 ||
-        o.kernel > STENCIL_KERNEL_TC || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0)
+        o.kernel > STENCIL_KERNEL_TC_UMMA || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0 ||
+        o.mma_n < 0)
         return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
 
     stencil_plan* p = new (std::nothrow) stencil_plan();
@@ -482,7 +604,7 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     }
 
     stencil_status_t st;
-    if (p->compute != STENCIL_COMPUTE_FP32 || o.kernel == STENCIL_KERNEL_TC) {
+    if (p->compute != STENCIL_COMPUTE_FP32 || o.kernel >= STENCIL_KERNEL_TC) {
         if (p->compute == STENCIL_COMPUTE_FP32) p->compute = STENCIL_COMPUTE_TC_TF32;
         st = configure_tc(p);
     } else if (o.kernel == STENCIL_KERNEL_NAIVE) {
@@ -543,6 +665,12 @@ stencil_status_t stencil_plan_info(const stencil_plan_t* p, stencil_plan_info_t*
     i.ctas = p->strips * p->tiles_y;
     i.smem_bytes = p->smem;
     i.workspace_bytes = (int64_t)((size_t)p->ny * p->nx * p->elem);
+    i.mma_n = p->umma_n;
+    if (p->umma_n) {
+        i.threads = box49_umma_threads();
+        i.ctas = p->umma_ctas;
+        i.smem_bytes = box49_umma_smem_bytes(p->compute == STENCIL_COMPUTE_TC_TF32, p->umma_n);
+    }
     *info = i;
     return STENCIL_OK;
 }
@@ -560,6 +688,12 @@ stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64
     cudaStream_t st = (cudaStream_t)stream;
     p->last_stream = st;
     const size_t bytes = (size_t)p->ny * p->nx * p->elem;
+    if (p->opt.autotune && !p->tuned && T > 0 &&
+        (p->kernel == STENCIL_KERNEL_TC || p->kernel == STENCIL_KERNEL_TC_UMMA)) {
+        stencil_status_t s = autotune_tc(p, in, st);
+        if (s != STENCIL_OK) return s;
+        p->tuned = 1;
+    }
     if (p->opt.autotune && !p->tuned && p->kernel == STENCIL_KERNEL_STREAM && T > 0) {
         stencil_status_t s = autotune(p, in, st);
         if (s != STENCIL_OK) return s;

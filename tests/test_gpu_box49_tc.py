@@ -52,7 +52,7 @@ def test_one_step_dyadic_exact(oracle, compute, dtype, shape, boundary):
     W[rng.random((7, 7)) < 0.3] = 0.0  # asymmetric, with holes
     u0 = (rng.integers(0, 256, size=shape) / 256.0).astype(np.float32)
     got, info = _run(u0, W, 1, compute, dtype, boundary)
-    assert info["kernel"] == 3
+    assert info["kernel"] in (3, 5)  # warp MMAs, or tcgen05 where it applies
     ref = oracle.sweep_f64(u0, W, 1, boundary)
     if dtype == "bf16":  # the stored result is rounded to BF16
         ref = torch.from_numpy(ref.astype(np.float32)).bfloat16().float().numpy()
@@ -83,7 +83,7 @@ def test_pipelined_equals_single_tile_kernel(compute, dtype, boundary):
     W = inputs.pattern_weights("box49")
     u0 = inputs.field(300, 520)
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
-    p = Plan(300, 520, W, dtype=dtype, boundary=boundary, compute=compute)
+    p = Plan(300, 520, W, dtype=dtype, boundary=boundary, compute=compute, kernel="tc_warp")
     x = torch.from_numpy(u0).to("cuda", tdt)
     a = p.run(x, 7)
     # the same grid at an offset of one element: rows are no longer 16-byte aligned
