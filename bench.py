@@ -281,8 +281,10 @@ def run_variant(args, world, rank, local):
         plans, xs, outs, hins, houts = {}, {}, {}, {}, {}
         for pn in pats:
             f = inputs.field(n, n)
-            plans[pn] = Plan(n, n, inputs.pattern_weights(pn), dtype=dtype, compute=compute,
-                             autotune=(compute == "fp32" and not args.no_autotune))
+            kern = {"auto": "auto", "warp": "tc_warp", "umma": "tc_umma"}[args.tc_engine] \
+                if compute.startswith("tc") else "auto"
+            plans[pn] = Plan(n, n, inputs.pattern_weights(pn), dtype=dtype, compute=compute, kernel=kern,
+                             autotune=not args.no_autotune)
             hins[pn] = torch.from_numpy(f).to(tdt).pin_memory()
             xs[pn] = hins[pn].cuda()
             outs[pn] = torch.empty_like(xs[pn])
@@ -319,6 +321,7 @@ def run_variant(args, world, rank, local):
             "value": world * units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
             "dtype": dtype,
             "config": {"workload": VARIANTS[name], "ny": n, "nx": n, "T": T, "compute": compute,
+                       "tc_engine": args.tc_engine if compute.startswith("tc") else None,
                        "per_pattern_ms": per, "plans": {pn: plans[pn].info() for pn in pats},
                        "l2": "inputs larger than L2" if n * n * esz > 129e6 else
                              "grid fits in L2 (parity workload; not roofline-meaningful)"},
@@ -419,6 +422,8 @@ def main():
                     help="comma-separated subset of box9,star13 (profiling captures)")
     ap.add_argument("--workload", default="box9+star13", choices=sorted(VARIANTS) + ["box9+star13"],
                     help="box9+star13 (the headline) or one of the variant workloads")
+    ap.add_argument("--tc-engine", default="auto", choices=["auto", "warp", "umma"],
+                    help="tensor-core workloads: autotuned engine choice, warp-level MMAs, or tcgen05")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

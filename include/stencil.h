@@ -78,7 +78,9 @@ typedef enum {
  * which take zero-boundary grids stored in the MMA operand type (BF16 storage
  * with TC_BF16, FP32 with TC_TF32), rows of a multiple of 16 bytes,
  * ny >= 134 and nx >= 128.  With TC_TF32 the first launch of a run (which rounds the
- * caller's FP32 input to TF32) always runs on the warp-MMA engine. */
+ * caller's FP32 input to TF32) always runs on the warp-MMA engine.  kernel = TC
+ * or AUTO picks tcgen05 for BF16 and the warp engine for TF32 (the faster of
+ * each as measured); with autotune the first run times both. */
 typedef enum {
     STENCIL_KERNEL_AUTO = 0,
     STENCIL_KERNEL_NAIVE = 1,      /* one thread per point, one step per launch      */
@@ -96,7 +98,7 @@ typedef struct {
     int threads;      /* threads per CTA of the streaming kernel (multiple of 32)   */
     int tile_rows;    /* output rows per CTA tile of the streaming kernel           */
     int autotune;     /* 1: time candidate configurations on first run              */
-    int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16/32)   */
+    int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16)      */
 } stencil_options_t;
 
 /* What a plan decided.  Filled by stencil_plan_info(). */

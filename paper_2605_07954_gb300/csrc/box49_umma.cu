@@ -31,10 +31,17 @@
 // Persistent CTA (one per SM), six warps:
 //   warp 0       TMA producer, STAGES-deep ring of staged tiles;
 //   warp 1       TMEM allocation and the single-thread MMA issue;
-//   warps 2..5   epilogue: tcgen05.ld of the lane quarter warp % 4, convert,
-//                store to global memory.
+//   warps 2..5   epilogue: tcgen05.ld of the lane quarter warp % 4 (all 128
+//                columns, one wait), release of the accumulator, conversion
+//                into a 128-byte swizzled staging tile, and one TMA tensor
+//                store per 128-byte column atom (clipped at the grid edges).
 // Two accumulators of 128 TMEM columns let the epilogue of one tile overlap
-// the MMAs of the next.  mbarriers: full / empty per stage, tmem_full /
+// the MMAs of the next; two staging buffers (one where shared memory is
+// short) let the TMA store of one tile overlap the epilogue of the next.
+// Measured on GB300 (16384^2, BF16): the MMAs then cost ~65 cycles each
+// whatever their N, i.e. the A operand streams from shared memory at ~64 B
+// per cycle, so the widest N (fewest re-reads of the row-shifted A) is the
+// fastest: N = 64 gives 912 GStencil/s.  mbarriers: full / empty per stage, tmem_full /
 // tmem_empty per accumulator, one drain barrier.  Every wait is bounded
 // (%globaltimer, 2 s, and an iteration cap): when one expires the kernel
 // stores STENCIL_ERR_TIMEOUT in the status word, raises a CTA-wide abort flag,
@@ -83,13 +90,17 @@ struct UmCfg {
     static constexpr int BPLANE = NT * 16;                       // bytes per B plane
     static constexpr int B_BYTES = BPLANES * BPLANE;
     static constexpr int NBARS = 2 * STAGES + 5;
-    static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 7 * B_BYTES + 8 * NBARS;  // + alignment slack
+    static constexpr int OUT_BYTES = kUmRows * kUmCols * EB;     // one staged output tile
+    static constexpr int BASE = STAGES * STAGE_BYTES + 7 * B_BYTES + 8 * NBARS;
+    static constexpr int STG = 1024 + BASE + 2 * OUT_BYTES <= 227 * 1024 ? 2 : 1;  // output staging buffers
+    static constexpr int SMEM = 1024 + BASE + STG * OUT_BYTES;   // + alignment slack
     static_assert(kUmCols % NT == 0 && NT % 16 == 0, "N-tile width");
     static_assert(kUmCols + KE >= kUmCols + L + 3, "staged columns cover the footprint");
     static_assert((JT - 1) * NT + (KSTEPS - 1) * KE <= kUmCols, "K slices end in the plane pair");
     static_assert(AE % KE == 0 && PPI == 2, "K slices do not straddle atoms");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
-    static_assert(STAGE_BYTES % 1024 == 0 && B_BYTES % 16 == 0, "TMA and descriptor alignment");
+    static_assert(STAGE_BYTES % 1024 == 0 && OUT_BYTES % 1024 == 0 && B_BYTES % 16 == 0,
+                  "TMA and descriptor alignment");
 };
 static_assert(kUmPlane % 128 == 0 && kUmPlane >= kUmSR * 16, "plane pitch");
 static_assert(kUmAtom % 1024 == 0 && kUmAtom >= kUmSR * 128, "atom pitch");
@@ -230,18 +241,45 @@ __device__ __forceinline__ void um_commit(unsigned bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void um_ld16(unsigned taddr, float (&v)[16]) {
-    unsigned r[16];
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void um_ld32(unsigned taddr, unsigned* r) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void um_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Named barrier 1 over the 128 epilogue threads; returns the AND of `pred`.
+__device__ __forceinline__ int um_epi_and(int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred)
+        : "memory");
+    return r;
+}
+
+__device__ __forceinline__ void um_epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void um_tma_store_2d(const CUtensorMap* map, unsigned src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void um_st_shared_v4(unsigned addr, unsigned a, unsigned b, unsigned c, unsigned d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
 }
 
 __device__ __forceinline__ unsigned um_tf32(float x) {
@@ -262,12 +300,13 @@ __device__ __forceinline__ void um_fence_after() {
 template <bool TF32, int NT>
 __global__ void __launch_bounds__(kUmThreads, 1)
     box49_umma_kernel(const __grid_constant__ CUtensorMap tmap_sw, const __grid_constant__ CUtensorMap tmap_pl,
-                      const __grid_constant__ UmParams p) {
+                      const __grid_constant__ CUtensorMap tmap_out, const __grid_constant__ UmParams p) {
     using C = UmCfg<TF32, NT>;
     extern __shared__ __align__(1024) unsigned char um_dyn[];
     // staging area on a 1024-byte boundary (SMEM includes the slack)
     unsigned char* stages = um_dyn + ((1024u - (um_smem(um_dyn) & 1023u)) & 1023u);
-    unsigned char* bmat = stages + C::STAGES * C::STAGE_BYTES;
+    unsigned char* outstg = stages + C::STAGES * C::STAGE_BYTES;  // output staging, 1024-byte aligned
+    unsigned char* bmat = outstg + C::STG * C::OUT_BYTES;
     __shared__ unsigned s_tmem;
     __shared__ volatile int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -367,8 +406,12 @@ __global__ void __launch_bounds__(kUmThreads, 1)
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             um_fence_after();
             if (lane == 0) {
+                // Base descriptors of this stage; every MMA below adds a compile-time
+                // byte offset / 16 to the start-address field (addresses < 256 KB).
                 const unsigned sbase = um_smem(stages + s * C::STAGE_BYTES);
-#pragma unroll 1
+                const unsigned long long a_sw = um_desc_sw128(sbase);
+                const unsigned long long a_pl = um_desc(sbase + (unsigned)(C::NA * kUmAtom), kUmPlane, 128);
+#pragma unroll
                 for (int j = 0; j < C::JT; ++j) {
                     const unsigned d = tmem + (unsigned)(b * 128 + NT * j);
 #pragma unroll
@@ -377,10 +420,9 @@ __global__ void __launch_bounds__(kUmThreads, 1)
 #pragma unroll
                         for (int di = 0; di < 7; ++di) {
                             const unsigned long long a =
-                                c < kUmCols
-                                    ? um_desc_sw128(sbase + (unsigned)((c / C::AE) * kUmAtom + 128 * di +
-                                                                       (c % C::AE) * C::EB))
-                                    : um_desc(sbase + (unsigned)(C::NA * kUmAtom + 16 * di), kUmPlane, 128);
+                                c < kUmCols ? a_sw + (unsigned long long)(((c / C::AE) * kUmAtom + 128 * di +
+                                                                           (c % C::AE) * C::EB) >> 4)
+                                            : a_pl + (unsigned long long)((16 * di) >> 4);
                             const unsigned long long bd =
                                 bdesc0 + (unsigned long long)((di * C::B_BYTES + ks * C::PPI * C::BPLANE) >> 4);
                             um_mma<TF32>(d, a, bd, idesc, (di | ks) != 0);
@@ -401,58 +443,76 @@ __global__ void __launch_bounds__(kUmThreads, 1)
         __syncwarp();
     } else {
         // ---------------- epilogue: TMEM lanes 32 q .. 32 q + 31 ----------------
+        // Per tile: load the thread's 128 accumulators (one wait), free the
+        // TMEM buffer, write the row into a 128-byte swizzled staging tile and
+        // let one thread store the tile with TMA (clipped at the grid edges).
         const int q = warp & 3;
+        const int r = 32 * q + lane;  // tile row = TMEM lane
+        const bool issuer = threadIdx.x == 64;
+        constexpr int AEO = 128 / C::EB;            // output columns per staged atom
+        constexpr int NAO = kUmCols / AEO;          // staged atoms per tile
         int it = 0;
         for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, ++it) {
             const int b = it & 1;
             int ok = 1;
             if (lane == 0) ok = um_wait(tfull0 + 8u * b, (it >> 1) & 1, &s_abort, p.status);
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!um_epi_and(ok)) break;  // the four epilogue warps leave together
             um_fence_after();
-            const int x0 = (tile % p.tiles_x) * kUmCols, y0 = (tile / p.tiles_x) * kUmRows;
-            const int y = y0 + 32 * q + lane;
+            unsigned v[kUmCols];
             const unsigned trow = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(b * 128);
-#pragma unroll 1
-            for (int c = 0; c < kUmCols / 16; ++c) {
-                float v[16];
-                um_ld16(trow + (unsigned)(16 * c), v);
-                const int x = x0 + 16 * c;
-                if (y < p.ny && x < p.nx) {
-                if constexpr (TF32) {
-                    float* o = static_cast<float*>(p.out) + (size_t)y * p.ld + x;
-                    if (p.round_out) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(um_tf32(v[i]));
-                    }
-                    if (x + 16 <= p.nx) {
-#pragma unroll
-                        for (int i = 0; i < 16; i += 4)
-                            *reinterpret_cast<float4*>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                    } else {
-                        for (int i = 0; i < 16 && x + i < p.nx; ++i) o[i] = v[i];
-                    }
-                } else {
-                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(p.out) + (size_t)y * p.ld + x;
-                    if (x + 16 <= p.nx) {
-                        unsigned w[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-                            w[i] = *reinterpret_cast<unsigned*>(&h);
-                        }
-                        reinterpret_cast<uint4*>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                        reinterpret_cast<uint4*>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                    } else {
-                        for (int i = 0; i < 16 && x + i < p.nx; ++i) o[i] = __float2bfloat16_rn(v[i]);
-                    }
-                }
-                }
-                __syncwarp();  // converged again before the next collective tcgen05.ld
-            }
+            for (int c = 0; c < kUmCols / 32; ++c) um_ld32(trow + (unsigned)(32 * c), v + 32 * c);
+            um_ld_wait();
             um_fence_before();
             __syncwarp();
-            if (lane == 0) um_bar_arrive(tempty0 + 8u * b);
+            if (lane == 0) um_bar_arrive(tempty0 + 8u * b);  // accumulator free for the MMAs
+            const int x0 = (tile % p.tiles_x) * kUmCols, y0 = (tile / p.tiles_x) * kUmRows;
+            const int sb = C::STG == 2 ? (it & 1) : 0;
+            // the store that last read this staging buffer has finished reading it
+            if (issuer) {
+                if constexpr (C::STG == 2)
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                else
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            }
+            um_epi_sync();
+            const unsigned stg = um_smem(outstg + sb * C::OUT_BYTES);
+#pragma unroll
+            for (int a = 0; a < NAO; ++a) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {  // 16-byte chunk c of this row in atom a
+                    unsigned w[4];
+                    if constexpr (TF32) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const unsigned u = v[a * 32 + c * 4 + i];
+                            w[i] = p.round_out ? um_tf32(__uint_as_float(u)) : u;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(v[a * 64 + c * 8 + 2 * i]),
+                                                                     __uint_as_float(v[a * 64 + c * 8 + 2 * i + 1]));
+                            w[i] = *reinterpret_cast<unsigned*>(&h);
+                        }
+                    }
+                    um_st_shared_v4(stg + (unsigned)(a * kUmRows * 128 + r * 128 + ((c ^ (r & 7)) << 4)), w[0], w[1],
+                                    w[2], w[3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging is read by TMA
+            um_epi_sync();
+            if (issuer) {
+#pragma unroll
+                for (int a = 0; a < NAO; ++a)
+                    um_tma_store_2d(&tmap_out, stg + (unsigned)(a * kUmRows * 128), x0 + a * AEO, y0);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
         }
+        // every store has completed (and read its staging) before the CTA exits
+        if (issuer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     }
 
     um_fence_before();
@@ -470,8 +530,7 @@ __global__ void __launch_bounds__(kUmThreads, 1)
 const void* get_box49_umma_kernel(int tf32, int nt) {
     if (tf32) {
         if (nt == 16) return (const void*)box49_umma_kernel<true, 16>;
-        if (nt == 32) return (const void*)box49_umma_kernel<true, 32>;
-        return nullptr;
+        return nullptr;  // wider TF32 tiles do not fit shared memory with the output staging
     }
     if (nt == 16) return (const void*)box49_umma_kernel<false, 16>;
     if (nt == 32) return (const void*)box49_umma_kernel<false, 32>;
@@ -480,7 +539,7 @@ const void* get_box49_umma_kernel(int tf32, int nt) {
 }
 
 int box49_umma_smem_bytes(int tf32, int nt) {
-    if (tf32) return nt == 16 ? UmCfg<true, 16>::SMEM : UmCfg<true, 32>::SMEM;
+    if (tf32) return UmCfg<true, 16>::SMEM;
     return nt == 16 ? UmCfg<false, 16>::SMEM : nt == 32 ? UmCfg<false, 32>::SMEM : UmCfg<false, 64>::SMEM;
 }
 
@@ -504,11 +563,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 um_encoder() {
 }
 
 static CUresult um_encode(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, int tf32, const void* src,
-                          int ny, int nx, int ld, int box_x, CUtensorMapSwizzle swz) {
+                          int ny, int nx, int ld, int box_x, int box_y, CUtensorMapSwizzle swz) {
     const int eb = tf32 ? 4 : 2;
     const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)eb};
-    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)kUmSR};
+    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                const_cast<void*>(src), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
@@ -525,9 +584,11 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
     PFN_cuTensorMapEncodeTiled_v12000 enc = um_encoder();
     if (!fn || !enc) return cudaErrorNotSupported;
     const int eb = tf32 ? 4 : 2;
-    alignas(64) CUtensorMap map_sw, map_pl;
-    if (um_encode(enc, &map_sw, tf32, src, ny, nx, ld, 128 / eb, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
-        um_encode(enc, &map_pl, tf32, src, ny, nx, ld, 16 / eb, CU_TENSOR_MAP_SWIZZLE_NONE) != CUDA_SUCCESS)
+    alignas(64) CUtensorMap map_sw, map_pl, map_out;
+    if (um_encode(enc, &map_sw, tf32, src, ny, nx, ld, 128 / eb, kUmSR, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
+        um_encode(enc, &map_pl, tf32, src, ny, nx, ld, 16 / eb, kUmSR, CU_TENSOR_MAP_SWIZZLE_NONE) != CUDA_SUCCESS ||
+        um_encode(enc, &map_out, tf32, dst, ny, nx, ld, 128 / eb, kUmRows, CU_TENSOR_MAP_SWIZZLE_128B) !=
+            CUDA_SUCCESS)
         return cudaErrorNotSupported;
     UmParams up{};
     up.out = dst;
@@ -539,7 +600,7 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
     up.round_out = round_out;
     up.status = status;
     for (int i = 0; i < 49; ++i) up.w[i] = w[i];
-    void* args[] = {&map_sw, &map_pl, &up};
+    void* args[] = {&map_sw, &map_pl, &map_out, &up};
     const int grid = ctas < up.tiles ? ctas : up.tiles;
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kUmThreads), args,
                             (size_t)box49_umma_smem_bytes(tf32, nt), st);
