@@ -48,11 +48,12 @@ def _ncu_traffic(key: str):
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)
-        for path, sha in rec["sources_sha256"].items():
+        ent = rec["kernels"].get(key, {})
+        for path, sha in ent.get("sources_sha256", rec["sources_sha256"]).items():
             with open(os.path.join(ROOT, path), "rb") as g:
                 if hashlib.sha256(g.read()).hexdigest() != sha:
                     return None
-        return rec["kernels"].get(key, {}).get("traffic_bytes")
+        return ent.get("traffic_bytes")
     except (OSError, KeyError, ValueError):
         return None
 
@@ -330,7 +331,10 @@ def run_variant(args, world, rank, local):
                                        "peak_gbs": peaks["hbm_gbs"],
                                        "frac": alg_bytes / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                        "note": f"{2 * esz} B per point-step x {k} steps per launch "
-                                               f"({pats[0]})"},
+                                               f"({pats[0]})",
+                                       "traffic": _ncu_traffic(
+                                           f"box49_{'umma' if info0['kernel'] == 5 else 'warp'}_{dtype}_{n}")
+                                       if compute.startswith("tc") else None},
             "e2e": {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GStencil/s",
                     "h2d_bytes_per_step": len(pats) * n * n * esz, "d2h_bytes_per_step": len(pats) * n * n * esz,
                     "api": "Plan.run (stencil_run) with torch copies of pinned host grids"},
