@@ -41,6 +41,10 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def peaks_hbm() -> float:
+    return _peaks()[0]["hbm_gbs"]
+
+
 def _ncu_traffic(key: str):
     """DRAM bytes per launch of `key` from the committed ncu capture, if the
     kernel sources are unchanged since it was taken; else None."""
@@ -196,6 +200,9 @@ VARIANTS = {
     "box49-tc-bf16": "Box-2D49P, 16384x16384, 200 steps, BF16 storage, BF16 tensor-core contraction, FP32 accumulate",
     "box9+star13-bf16": "Box-2D9P and Star-2D13P, 8192x8192, 1000 steps each, BF16 storage, FP32 arithmetic",
     "heat512": "Heat-2D 5-point (weights 0.2f), 512x512, 100 steps, FP32, zero boundary",
+    "scaling": "weak-scaling sweep of the paper's shape: Heat-5 (Star-2D5P), Box-9, Star-13 and Box-49 FP32 "
+               "on square grids 128^2 .. 32768^2, 1000 steps each, plus Star-2D5P on 44800^2 (HBM "
+               "roofline point); inputs tile the seeded 4096^2 field",
 }
 
 # (pattern list, n, T, dtype, compute) of the single-plan variants
@@ -342,6 +349,48 @@ def run_variant(args, world, rank, local):
         })
         for pn in pats:
             plans[pn].close()
+    if name == "scaling":
+        from paper_2605_07954_gb300 import Plan
+        T = 1000
+        base = torch.from_numpy(inputs.field(4096, 4096)).cuda()
+        sizes = [2 ** e for e in range(7, 16)]
+        runs = [(pn, n) for pn in ("heat5", "box9", "star13", "box49") for n in sizes] + [("heat5", 44800)]
+        table, total_ms, total_units, launches = [], 0.0, 0.0, 0
+        sampler = ClockSampler(gpu_id)
+        sampler.start()
+        for pn, n in runs:
+            reps = -(-n // 4096)
+            x = base.repeat(reps, reps)[:n, :n].contiguous()
+            out = torch.empty_like(x)
+            plan = Plan(n, n, inputs.pattern_weights(pn), autotune=not args.no_autotune)
+            ms = _time_steps(lambda: plan.run(x, T, out=out), 1, 3 if n <= 4096 else 1, stream)
+            plan.status()
+            info = plan.info()
+            units = float(n) * n * T
+            gst = units / (ms * 1e-3) / 1e9
+            table.append({"pattern": pn, "n": n, "ms": ms, "gstencil_s": gst, "k": info["tb_depth"],
+                          "threads": info["threads"],
+                          "hbm_effective_frac": gst * 8.0 / peaks_hbm() if n * n * 4 > 129e6 else None})
+            total_ms += ms
+            total_units += units
+            launches += plan.launches(T)
+            plan.close()
+            del x, out
+            torch.cuda.empty_cache()
+        clocks = sampler.stop()
+        ms = _max_over_ranks(world, total_ms)
+        line.update({
+            "metric": "GStencil/s (weak-scaling sweep: 4 patterns x 128^2..32768^2 + Star-2D5P 44800^2, "
+                      "1000 steps each)",
+            "value": world * total_units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
+            "dtype": "f32",
+            "config": {"workload": VARIANTS[name], "T": T, "table": table,
+                       "l2": "grids up to 4096^2 fit in L2 (launch- and latency-bound); larger ones stream "
+                             "from HBM (hbm_effective_frac: 8 B per point-step / measured copy bandwidth)"},
+            "gpu_launches": launches,
+            "e2e": None,
+            "clocks": clocks,
+        })
     if name == "adjoint":
         from paper_2605_07954_gb300 import Plan, adjoint
         n, T = 4096, 512
