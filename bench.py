@@ -198,6 +198,8 @@ VARIANTS = {
     "box49-bf16": "Box-2D49P, 16384x16384, 200 steps, BF16 storage, FP32 CUDA-core arithmetic",
     "box49-tc-tf32": "Box-2D49P, 16384x16384, 200 steps, FP32 storage, TF32 tensor-core contraction, FP32 accumulate",
     "box49-tc-bf16": "Box-2D49P, 16384x16384, 200 steps, BF16 storage, BF16 tensor-core contraction, FP32 accumulate",
+    "box49-tc-3xtf32": "Box-2D49P, 16384x16384, 200 steps, FP32 storage, 3xTF32 tensor-core contraction "
+                       "(split hi/lo operands, FP32-level accuracy), FP32 accumulate",
     "box9+star13-bf16": "Box-2D9P and Star-2D13P, 8192x8192, 1000 steps each, BF16 storage, FP32 arithmetic",
     "heat512": "Heat-2D 5-point (weights 0.2f), 512x512, 100 steps, FP32, zero boundary",
     "scaling": "weak-scaling sweep of the paper's shape: Heat-5 (Star-2D5P), Box-9, Star-13 and Box-49 FP32 "
@@ -211,6 +213,7 @@ _PLAN_VARIANTS = {
     "box49-bf16": (("box49",), 16384, 200, "bf16", "fp32"),
     "box49-tc-tf32": (("box49",), 16384, 200, "f32", "tc_tf32"),
     "box49-tc-bf16": (("box49",), 16384, 200, "bf16", "tc_bf16"),
+    "box49-tc-3xtf32": (("box49",), 16384, 200, "f32", "tc_3xtf32"),
     "box9+star13-bf16": (("box9", "star13"), 8192, 1000, "bf16", "fp32"),
     "heat512": (("heat5",), 512, 100, "f32", "fp32"),
 }

@@ -61,15 +61,19 @@ typedef enum { STENCIL_BOUNDARY_ZERO = 0, STENCIL_BOUNDARY_PERIODIC = 1 } stenci
 
 /* Arithmetic engine.  AUTO and FP32 use the CUDA cores.  The tensor-core
  * engines treat each weight row of a radius-3 (7x7) stencil as a banded
- * Toeplitz matrix and run the step as warp MMAs with FP32 accumulation
- * (Sec. II-D's stencil-as-matrix-product idea): TC_TF32 rounds inputs and
- * weights to TF32, TC_BF16 to BF16 (both round-to-nearest-even).  Storage
- * FP32 or BF16.  Other radii or FP16 storage: STENCIL_ERR_UNSUPPORTED. */
+ * Toeplitz matrix and run the step as MMAs with FP32 accumulation (Sec.
+ * II-D's stencil-as-matrix-product idea): TC_TF32 rounds inputs and weights
+ * to TF32, TC_BF16 to BF16 (both round-to-nearest-even).  TC_3XTF32 recovers
+ * accuracy: inputs and weights split into TF32 hi + lo parts and each
+ * product is hi*hi + hi*lo + lo*hi (three MMAs, FP32-level error; warp-MMA
+ * engine, FP32 storage only).  Storage FP32 or BF16.  Other radii or FP16
+ * storage: STENCIL_ERR_UNSUPPORTED. */
 typedef enum {
     STENCIL_COMPUTE_AUTO = 0,
     STENCIL_COMPUTE_FP32 = 1,
     STENCIL_COMPUTE_TC_TF32 = 2,
-    STENCIL_COMPUTE_TC_BF16 = 3
+    STENCIL_COMPUTE_TC_BF16 = 3,
+    STENCIL_COMPUTE_TC_3XTF32 = 4
 } stencil_compute_t;
 
 /* Kernel family.  The tensor-core contraction (7x7 box, one step per launch)

@@ -22,6 +22,11 @@
 //         two MMAs per (tile, di).
 //   BF16: m16n8k16, inputs and weights rounded to BF16 (RN-even); one MMA per
 //         (tile, di).
+//   3xTF32 (accuracy recovery): FP32 storage staged unrounded; every A
+//         fragment and weight splits into x = hi + lo with hi = tf32(x),
+//         lo = tf32(x - hi), and each product is hi*hi + hi*lo + lo*hi (the
+//         lo*lo term, ~2^-22 relative, is dropped), the two small products
+//         accumulated first.  Six MMAs per (tile, di); error near FP32.
 // CTA: 8 warps, 128x128 outputs; warp w owns rows 16w..16w+15 and all 16
 // column tiles.  The staged tile is (128+6) x (128+8) elements, with a row
 // pitch padded so the 8 row addresses of every ldmatrix fall in distinct banks.
@@ -106,6 +111,24 @@ __device__ __forceinline__ void make_bfrag(const TcParams& p, int g, int t, unsi
     }
 }
 
+// 3xTF32: hi / lo parts of the Toeplitz B fragments (TF32 layout).
+__device__ __forceinline__ void make_bfrag_split(const TcParams& p, int g, int t, unsigned (&bhi)[7][4],
+                                                 unsigned (&blo)[7][4]) {
+    auto bw = [&](int di, int k, int n) -> float {
+        const int dj = k - n - 1;
+        return (dj >= 0 && dj <= 6) ? p.w[di * 7 + dj] : 0.f;
+    };
+#pragma unroll
+    for (int di = 0; di < 7; ++di) {
+        const float v[4] = {bw(di, t, g), bw(di, t + 4, g), bw(di, t + 8, g), bw(di, t + 12, g)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            bhi[di][i] = f32_to_tf32(v[i]);
+            blo[di][i] = f32_to_tf32(v[i] - __uint_as_float(bhi[di][i]));
+        }
+    }
+}
+
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
@@ -166,6 +189,62 @@ __device__ __forceinline__ void tile_mma(const void* stile, int warp, int lane, 
     }
 }
 
+// 3xTF32: as the TF32 branch of tile_mma, on unrounded FP32 staging.  An MMA
+// adds into its accumulator with truncation, which biases a running sum, so
+// every hi*hi MMA (8 products) starts from a zero accumulator and is added to
+// the running sum with a round-to-nearest FP32 add; the two small correction
+// products of a (tile, di), ~2^-11 of the result, share one accumulator.
+__device__ __forceinline__ void tile_mma_split(const void* stile, int warp, int lane, const unsigned (&bhi)[7][4],
+                                               const unsigned (&blo)[7][4], float (&acc)[16][4]) {
+    const int r0 = 16 * warp;
+#pragma unroll
+    for (int di = 0; di < 7; ++di) {
+        const int m = lane >> 3;
+        const int row = r0 + di + (lane & 7) + 8 * (m & 1);
+        const unsigned base = (unsigned)__cvta_generic_to_shared(
+            static_cast<const unsigned*>(stile) + row * kTcPitchF32 + 4 * (m >> 1));
+        float small[2][4];  // tile j's correction terms live in small[j & 1] for two steps
+        unsigned raw[2][4];
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(raw[0][0]), "=r"(raw[0][1]), "=r"(raw[0][2]), "=r"(raw[0][3]) : "r"(base));
+#pragma unroll
+        for (int j = 0; j <= 16; ++j) {
+            if (j < 16) {
+                asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                             : "=r"(raw[(j + 1) & 1][0]), "=r"(raw[(j + 1) & 1][1]), "=r"(raw[(j + 1) & 1][2]),
+                               "=r"(raw[(j + 1) & 1][3])
+                             : "r"(base + 32 * (j + 1)));
+            }
+            unsigned hi[4], lo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float x = __uint_as_float(raw[j & 1][i]);
+                hi[i] = f32_to_tf32(x);
+                lo[i] = f32_to_tf32(x - __uint_as_float(hi[i]));
+            }
+            if (j < 16) {  // K rows 0..7 of tile j
+                float (&sj)[4] = small[j & 1];
+                sj[0] = sj[1] = sj[2] = sj[3] = 0.f;
+                mma_tf32(sj, lo, bhi[di][0], bhi[di][1]);
+                mma_tf32(sj, hi, blo[di][0], blo[di][1]);
+                float big[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_tf32(big, hi, bhi[di][0], bhi[di][1]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[j][i] = __fadd_rn(acc[j][i], big[i]);
+            }
+            if (j > 0) {  // K rows 8..15 of tile j-1, which completes its row-di terms
+                float (&sk)[4] = small[(j - 1) & 1];
+                mma_tf32(sk, lo, bhi[di][2], bhi[di][3]);
+                mma_tf32(sk, hi, blo[di][2], blo[di][3]);
+                float big[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_tf32(big, hi, bhi[di][2], bhi[di][3]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[j - 1][i] = __fadd_rn(__fadd_rn(acc[j - 1][i], big[i]), sk[i]);
+            }
+        }
+    }
+}
+
 // C fragment rows g, g+8; columns 2t, 2t+1 of each of the 16 column tiles.
 template <typename TS>
 __device__ __forceinline__ void store_tile(const TcParams& p, float (&acc)[16][4], int x0, int y0, int r0,
@@ -207,8 +286,9 @@ __device__ __forceinline__ void store_tile(const TcParams& p, float (&acc)[16][4
 
 // ---- one tile per CTA, conversion while staging (any layout) ----------------------
 
-template <typename TS, bool BF16MMA>
+template <typename TS, bool BF16MMA, bool SPLIT = false>
 __global__ void __launch_bounds__(256) box49_tc_kernel(const __grid_constant__ TcParams p) {
+    static_assert(!SPLIT || (!BF16MMA && sizeof(TS) == 4), "3xTF32 takes FP32 storage");
     extern __shared__ float4 smem_f4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -259,6 +339,9 @@ __global__ void __launch_bounds__(256) box49_tc_kernel(const __grid_constant__ T
                 raw.x = *reinterpret_cast<unsigned*>(&a);
                 raw.y = *reinterpret_cast<unsigned*>(&b);
                 *reinterpret_cast<uint2*>(s16 + rr[u] * kTcPitchB16 + 4 * qq[u]) = raw;
+            } else if constexpr (SPLIT) {  // unrounded: the MMA loop splits hi / lo
+                *reinterpret_cast<float4*>(s32 + rr[u] * kTcPitchF32 + 4 * qq[u]) =
+                    make_float4(v[u][0], v[u][1], v[u][2], v[u][3]);
             } else {
                 *reinterpret_cast<uint4*>(s32 + rr[u] * kTcPitchF32 + 4 * qq[u]) =
                     make_uint4(f32_to_tf32(v[u][0]), f32_to_tf32(v[u][1]), f32_to_tf32(v[u][2]),
@@ -266,24 +349,32 @@ __global__ void __launch_bounds__(256) box49_tc_kernel(const __grid_constant__ T
             }
         }
     }
-    unsigned bfr[7][4];
-    make_bfrag<BF16MMA>(p, g, t, bfr);
-    __syncthreads();
-
     float acc[16][4];
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    tile_mma<BF16MMA>(BF16MMA ? (const void*)s16 : (const void*)s32, warp, lane, bfr, acc);
-    // FP32 storage, TF32 engine: intermediate states stay TF32-rounded, as
-    // the pipelined and tcgen05 engines expect (rounding at load is idempotent).
-    store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, !BF16MMA && sizeof(TS) == 4 && p.round_out);
+    if constexpr (SPLIT) {
+        unsigned bhi[7][4], blo[7][4];
+        make_bfrag_split(p, g, t, bhi, blo);
+        __syncthreads();
+        tile_mma_split(s32, warp, lane, bhi, blo, acc);
+        store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, false);
+    } else {
+        unsigned bfr[7][4];
+        make_bfrag<BF16MMA>(p, g, t, bfr);
+        __syncthreads();
+        tile_mma<BF16MMA>(BF16MMA ? (const void*)s16 : (const void*)s32, warp, lane, bfr, acc);
+        // FP32 storage, TF32 engine: intermediate states stay TF32-rounded, as
+        // the pipelined and tcgen05 engines expect (rounding at load is idempotent).
+        store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, !BF16MMA && sizeof(TS) == 4 && p.round_out);
+    }
 }
 
 // ---- persistent, double-buffered (16-byte aligned rows) ---------------------------
 
-template <typename TS, bool BF16MMA>
+template <typename TS, bool BF16MMA, bool SPLIT = false>
 __global__ void __launch_bounds__(256) box49_tc_pipe_kernel(const __grid_constant__ TcParams p) {
     static_assert(sizeof(TS) == (BF16MMA ? 2 : 4), "pipelined engine needs matching storage");
+    static_assert(!SPLIT || !BF16MMA, "3xTF32 splits FP32 operands");
     constexpr int CB = 4 * (int)sizeof(TS);  // bytes per 4-element group
     constexpr int PITCH_B = BF16MMA ? kTcPitchB16 * 2 : kTcPitchF32 * 4;
     constexpr int STAGE_B = kTcSR * PITCH_B;
@@ -293,8 +384,13 @@ __global__ void __launch_bounds__(256) box49_tc_pipe_kernel(const __grid_constan
     const int g = lane >> 2, t = lane & 3;
     const TS* gin = static_cast<const TS*>(p.in);
 
-    unsigned bfr[7][4];
-    make_bfrag<BF16MMA>(p, g, t, bfr);
+    // B fragments: one set, or hi / lo for 3xTF32 (the unused set stays empty).
+    unsigned bfr[7][4], blo[SPLIT ? 7 : 1][4];
+    if constexpr (SPLIT) {
+        make_bfrag_split(p, g, t, bfr, blo);
+    } else {
+        make_bfrag<BF16MMA>(p, g, t, bfr);
+    }
 
     // Copy tile `tile`'s groups into stage `st`; out-of-grid groups are zero-filled.
     auto issue = [&](int tile, int st) {
@@ -343,7 +439,7 @@ __global__ void __launch_bounds__(256) box49_tc_pipe_kernel(const __grid_constan
         }
         __syncthreads();
         char* stage = smem + st * STAGE_B;
-        if constexpr (!BF16MMA) {
+        if constexpr (!BF16MMA && !SPLIT) {
             if (p.convert_in) {  // the caller's FP32 input: round to TF32 in place
                 for (int i = tid; i < kTcSR * kTcQPR; i += 256) {
                     const int rr = i / kTcQPR, qq = i % kTcQPR;
@@ -358,14 +454,21 @@ __global__ void __launch_bounds__(256) box49_tc_pipe_kernel(const __grid_constan
         float acc[16][4];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-        tile_mma<BF16MMA>(stage, warp, lane, bfr, acc);
+        if constexpr (SPLIT) {
+            tile_mma_split(stage, warp, lane, bfr, blo, acc);
+        } else {
+            tile_mma<BF16MMA>(stage, warp, lane, bfr, acc);
+        }
         const int x0 = (tile % p.tiles_x) * kTcCols, y0 = (tile / p.tiles_x) * kTcRows;
-        store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, !BF16MMA && p.round_out);
+        store_tile<TS>(p, acc, x0, y0, 16 * warp, g, t, !BF16MMA && !SPLIT && p.round_out);
         __syncthreads();  // every warp is done with `stage` before it is refilled
     }
 }
 
-const void* get_box49_tc_kernel(int dtype, int bf16mma) {
+// engine: 0 = TF32, 1 = BF16, 2 = 3xTF32 (FP32 storage only).
+const void* get_box49_tc_kernel(int dtype, int engine) {
+    if (engine == 2) return dtype == DT_F32 ? (const void*)box49_tc_kernel<float, false, true> : nullptr;
+    const bool bf16mma = engine == 1;
     if (dtype == DT_F32) return bf16mma ? (const void*)box49_tc_kernel<float, true>
                                         : (const void*)box49_tc_kernel<float, false>;
     if (dtype == DT_BF16) return bf16mma ? (const void*)box49_tc_kernel<__nv_bfloat16, true>
@@ -374,14 +477,15 @@ const void* get_box49_tc_kernel(int dtype, int bf16mma) {
 }
 
 // The pipelined kernel for the matching storage/engine pairs, else nullptr.
-const void* get_box49_tc_pipe_kernel(int dtype, int bf16mma) {
-    if (dtype == DT_F32 && !bf16mma) return (const void*)box49_tc_pipe_kernel<float, false>;
-    if (dtype == DT_BF16 && bf16mma) return (const void*)box49_tc_pipe_kernel<__nv_bfloat16, true>;
+const void* get_box49_tc_pipe_kernel(int dtype, int engine) {
+    if (dtype == DT_F32 && engine == 0) return (const void*)box49_tc_pipe_kernel<float, false>;
+    if (dtype == DT_F32 && engine == 2) return (const void*)box49_tc_pipe_kernel<float, false, true>;
+    if (dtype == DT_BF16 && engine == 1) return (const void*)box49_tc_pipe_kernel<__nv_bfloat16, true>;
     return nullptr;
 }
 
-int box49_tc_smem_bytes(int bf16mma) {
-    return bf16mma ? kTcSR * kTcPitchB16 * 2 : kTcSR * kTcPitchF32 * 4;
+int box49_tc_smem_bytes(int engine) {
+    return engine == 1 ? kTcSR * kTcPitchB16 * 2 : kTcSR * kTcPitchF32 * 4;
 }
 
 }  // namespace gbst

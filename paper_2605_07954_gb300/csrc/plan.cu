@@ -31,9 +31,9 @@ GBST_DECL_STREAM(2, f32) GBST_DECL_STREAM(2, bf16) GBST_DECL_STREAM(2, f16)
 GBST_DECL_STREAM(3, f32) GBST_DECL_STREAM(3, bf16) GBST_DECL_STREAM(3, f16)
 #undef GBST_DECL_STREAM
 const void* get_naive_kernel(int radius, int dtype);
-const void* get_box49_tc_kernel(int dtype, int bf16mma);
-const void* get_box49_tc_pipe_kernel(int dtype, int bf16mma);
-int box49_tc_smem_bytes(int bf16mma);
+const void* get_box49_tc_kernel(int dtype, int engine);       // engine: 0 TF32, 1 BF16, 2 3xTF32
+const void* get_box49_tc_pipe_kernel(int dtype, int engine);
+int box49_tc_smem_bytes(int engine);
 const void* get_box49_umma_kernel(int tf32, int nt);
 int box49_umma_smem_bytes(int tf32, int nt);
 int box49_umma_threads();
@@ -236,7 +236,8 @@ static stencil_status_t configure_umma(stencil_plan* p) {
     if (want == STENCIL_KERNEL_TC_WARP) return STENCIL_OK;
     const int tf32 = p->compute == STENCIL_COMPUTE_TC_TF32;
     const char* why = nullptr;
-    if (p->boundary != STENCIL_BOUNDARY_ZERO) why = "the tcgen05 engine takes zero-boundary grids";
+    if (p->compute == STENCIL_COMPUTE_TC_3XTF32) why = "the tcgen05 engine runs TF32 and BF16 operands only";
+    else if (p->boundary != STENCIL_BOUNDARY_ZERO) why = "the tcgen05 engine takes zero-boundary grids";
     else if (tf32 ? p->dtype != STENCIL_F32 : p->dtype != STENCIL_BF16)
         why = "the tcgen05 engine needs FP32 storage for TF32 and BF16 storage for BF16";
     else if ((p->nx * (int64_t)p->elem) % 16 != 0) why = "the tcgen05 engine needs rows of a multiple of 16 bytes";
@@ -272,8 +273,10 @@ static stencil_status_t configure_umma(stencil_plan* p) {
 static stencil_status_t configure_tc(stencil_plan* p) {
     if (p->R != 3) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engines need radius 3 (7x7 weights)");
     if (p->dtype == STENCIL_F16) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core engines take FP32 or BF16 storage");
-    const int bf16 = p->compute == STENCIL_COMPUTE_TC_BF16;
-    p->naive = get_box49_tc_kernel(p->dtype, bf16);
+    const int engine = p->compute == STENCIL_COMPUTE_TC_BF16 ? 1 : p->compute == STENCIL_COMPUTE_TC_3XTF32 ? 2 : 0;
+    if (engine == 2 && p->dtype != STENCIL_F32)
+        return fail(STENCIL_ERR_UNSUPPORTED, "3xTF32 splits FP32 values: it takes FP32 storage");
+    p->naive = get_box49_tc_kernel(p->dtype, engine);
     if (!p->naive) return fail(STENCIL_ERR_UNSUPPORTED, "no tensor-core kernel for this dtype");
     p->kernel = STENCIL_KERNEL_TC;
     p->k = 1;
@@ -283,9 +286,9 @@ static stencil_status_t configure_tc(stencil_plan* p) {
     p->by = 128;
     p->strips = (int)ceil_div(p->nx, 128);
     p->tiles_y = (int)ceil_div(p->ny, 128);
-    p->smem = box49_tc_smem_bytes(bf16);
+    p->smem = box49_tc_smem_bytes(engine);
     CK(cudaFuncSetAttribute(p->naive, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem));
-    p->tc_pipe = p->nx % 4 == 0 ? get_box49_tc_pipe_kernel(p->dtype, bf16) : nullptr;
+    p->tc_pipe = p->nx % 4 == 0 ? get_box49_tc_pipe_kernel(p->dtype, engine) : nullptr;
     if (p->tc_pipe) {
         p->tc_pipe_smem = 2 * p->smem;
         CK(cudaFuncSetAttribute(p->tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc_pipe_smem));
@@ -558,7 +561,7 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
         return fail(STENCIL_ERR_INVALID_ARG, "bad boundary");
     stencil_options_t o{};
     if (opt) o = *opt;
-    if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_BF16 || o.kernel < 0 ||
+    if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_3XTF32 || o.kernel < 0 ||
         o.kernel > STENCIL_KERNEL_TC_UMMA || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0 ||
         o.mma_n < 0)
         return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
@@ -570,7 +573,8 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     p->R = radius;
     p->dtype = dtype;
     p->boundary = boundary;
-    p->compute = (o.compute == STENCIL_COMPUTE_TC_TF32 || o.compute == STENCIL_COMPUTE_TC_BF16)
+    p->compute = (o.compute == STENCIL_COMPUTE_TC_TF32 || o.compute == STENCIL_COMPUTE_TC_BF16 ||
+                  o.compute == STENCIL_COMPUTE_TC_3XTF32)
                      ? o.compute : STENCIL_COMPUTE_FP32;
     p->opt = o;
     p->elem = elem_size(dtype);

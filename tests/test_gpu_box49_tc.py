@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-ENGINES = [("tc_tf32", "f32"), ("tc_bf16", "bf16"), ("tc_bf16", "f32"), ("tc_tf32", "bf16")]
+ENGINES = [("tc_tf32", "f32"), ("tc_bf16", "bf16"), ("tc_bf16", "f32"), ("tc_tf32", "bf16"),
+           ("tc_3xtf32", "f32")]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -60,7 +61,8 @@ def test_one_step_dyadic_exact(oracle, compute, dtype, shape, boundary):
 
 
 @pytest.mark.parametrize("compute,dtype,gate", [("tc_tf32", "f32", 2e-3), ("tc_bf16", "bf16", 2e-2),
-                                                ("tc_bf16", "f32", 2e-2), ("tc_tf32", "bf16", 2e-2)])
+                                                ("tc_bf16", "f32", 2e-2), ("tc_tf32", "bf16", 2e-2),
+                                                ("tc_3xtf32", "f32", 1e-5)])
 def test_multistep_error_vs_oracle(oracle, compute, dtype, gate):
     W = inputs.pattern_weights("box49")
     u0 = inputs.field(300, 517)
@@ -72,7 +74,7 @@ def test_multistep_error_vs_oracle(oracle, compute, dtype, gate):
     assert e2 <= gate
 
 
-@pytest.mark.parametrize("compute,dtype", [("tc_tf32", "f32"), ("tc_bf16", "bf16")])
+@pytest.mark.parametrize("compute,dtype", [("tc_tf32", "f32"), ("tc_bf16", "bf16"), ("tc_3xtf32", "f32")])
 @pytest.mark.parametrize("boundary", ["zero", "periodic"])
 def test_pipelined_equals_single_tile_kernel(compute, dtype, boundary):
     """The persistent double-buffered kernel (aligned rows) and the one-tile-per-CTA
@@ -104,10 +106,14 @@ def test_rejects_unsupported():
         Plan(64, 64, inputs.pattern_weights("box9"), compute="tc_tf32")
     with pytest.raises(StencilError, match="UNSUPPORTED"):
         Plan(64, 64, inputs.pattern_weights("box49"), dtype="f16", compute="tc_bf16")
+    with pytest.raises(StencilError, match="UNSUPPORTED"):
+        Plan(300, 392, inputs.pattern_weights("box49"), dtype="bf16", compute="tc_3xtf32")
+    with pytest.raises(StencilError, match="UNSUPPORTED"):
+        Plan(300, 392, inputs.pattern_weights("box49"), compute="tc_3xtf32", kernel="tc_umma")
 
 
 VARIANTS = [("fp32", "f32", 1e-5), ("fp32", "bf16", 1e-2), ("tc_tf32", "f32", 5e-2),
-            ("tc_bf16", "bf16", 5e-2)]
+            ("tc_bf16", "bf16", 5e-2), ("tc_3xtf32", "f32", 1e-5)]
 
 
 @pytest.mark.parametrize("compute,dtype,gate", VARIANTS)
@@ -130,3 +136,17 @@ def test_box49_16384_T200_variants(oracle, compute, dtype, gate):
           f"relLinf={errs[0][1]:.3e}; interior relL2={errs[1][0]:.3e} relLinf={errs[1][1]:.3e}")
     assert max(e[0] for e in errs) <= gate
     assert got.min() >= -1e-3 and got.max() <= u0.max() * (1 + 1e-2)
+
+
+def test_3xtf32_recovers_fp32_accuracy(oracle):
+    """Splitting operands into TF32 hi + lo parts brings the tensor-core error
+    from TF32 level down to that of the FP32 CUDA-core path (same order of
+    magnitude), 20 steps of Box-49 on a random field."""
+    W = inputs.pattern_weights("box49")
+    u0 = inputs.field(300, 520)
+    T = 20
+    ref = oracle.sweep_f64(u0, W, T)
+    errs = {c: rel_l2(_run(u0, W, T, c, "f32")[0], ref) for c in ("fp32", "tc_tf32", "tc_3xtf32")}
+    print("relL2 after 20 steps:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["tc_3xtf32"] <= 1e-2 * errs["tc_tf32"]
+    assert errs["tc_3xtf32"] <= max(20 * errs["fp32"], 1e-6)
