@@ -91,10 +91,18 @@ typedef enum {
     STENCIL_KERNEL_STREAM = 2,     /* row-streaming tiles, k steps per launch        */
     STENCIL_KERNEL_TC = 3,         /* tensor cores: tcgen05 where it applies, else warp MMA */
     STENCIL_KERNEL_TC_WARP = 4,    /* tensor cores, warp-MMA engine only             */
-    STENCIL_KERNEL_TC_UMMA = 5     /* tensor cores, tcgen05 engine (UNSUPPORTED where it does not apply) */
+    STENCIL_KERNEL_TC_UMMA = 5,    /* tensor cores, tcgen05 engine (UNSUPPORTED where it does not apply) */
+    STENCIL_KERNEL_RESIDENT = 6    /* small grids: the whole grid in one thread-block cluster's shared
+                                      memory, every step of a run in one launch                        */
 } stencil_kernel_t;
 
-/* Optional plan settings; pass NULL for defaults.  0 means "choose". */
+/* Optional plan settings; pass NULL for defaults.  0 means "choose".
+ * kernel = AUTO with FP32 arithmetic picks RESIDENT when the grid fits one
+ * cluster (two FP32 copies in the shared memory of at most 16 CTAs; roughly up
+ * to 700 x 700 for radius 1) and no streaming-kernel option (tb_depth,
+ * threads, tile_rows) is set; otherwise STREAM.  With autotune the first run
+ * times both.  stencil_plan_info reports tb_depth = 0 for RESIDENT (one
+ * launch per run), ctas = the cluster size and tile_rows = the slab height. */
 typedef struct {
     int compute;      /* stencil_compute_t                                          */
     int kernel;       /* stencil_kernel_t                                           */

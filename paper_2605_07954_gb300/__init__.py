@@ -18,7 +18,7 @@ from ._capi import StencilError, check
 DTYPES = {"f32": _capi.STENCIL_F32, "bf16": _capi.STENCIL_BF16, "f16": _capi.STENCIL_F16}
 BOUNDARIES = {"zero": _capi.STENCIL_BOUNDARY_ZERO, "periodic": _capi.STENCIL_BOUNDARY_PERIODIC}
 COMPUTES = {"auto": 0, "fp32": 1, "tc_tf32": 2, "tc_bf16": 3, "tc_3xtf32": 4}
-KERNELS = {"auto": 0, "naive": 1, "stream": 2, "tc": 3, "tc_warp": 4, "tc_umma": 5}
+KERNELS = {"auto": 0, "naive": 1, "stream": 2, "tc": 3, "tc_warp": 4, "tc_umma": 5, "resident": 6}
 
 
 def _torch_dtype_name(t) -> str:

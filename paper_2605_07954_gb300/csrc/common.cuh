@@ -43,6 +43,18 @@ struct StreamParams {
     WeightPairs w2;
 };
 
+// Parameters of the cluster-resident kernel (see sweep_resident.cu).
+struct ResidentParams {
+    const void* in;
+    void* out;
+    int ny, nx, ld;
+    int T;         // steps of this launch, >= 1
+    int periodic;  // 1: wrap; 0: zero outside the grid
+    int rp;        // slab rows per CTA
+    int pitch;     // floats per staged row (nx + 2R)
+    Weights w;
+};
+
 // ---- storage <-> FP32 ---------------------------------------------------------------
 
 template <typename TS> struct Storage;

@@ -39,6 +39,12 @@ int box49_umma_smem_bytes(int tf32, int nt);
 int box49_umma_threads();
 cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int ny, int nx, int ld,
                               int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st);
+const void* get_resident_kernel(int radius, int star, int dtype);
+int resident_threads();
+int resident_max_cluster();
+int resident_smem_bytes(int ny, int nx, int radius, int periodic, int C, int* rp_out);
+cudaError_t launch_resident(const void* fn, int C, int smem, const ResidentParams& prm, cudaStream_t st);
+bool resident_cluster_fits(const void* fn, int C, int smem);
 struct TcParams {  // must match box49_tc.cu
     const void* in;
     void* out;
@@ -86,6 +92,9 @@ struct stencil_plan {
     int umma_n = 0;     // tcgen05 engine in use: N of one MMA (0: warp-MMA engine)
     int umma_ok = 0;    // usable tcgen05 MMA widths, bit n / 16
     int umma_ctas = 0;
+    // cluster-resident kernel (sweep_resident.cu): usable cluster sizes (bit log2 C), the one in use
+    const void* res_fn = nullptr;
+    int res_ok = 0, res_c = 0, res_rp = 0, res_smem = 0;
     unsigned smem_set = 0;  // bit 2k+vec: that kernel's shared-memory attribute is set
     int tuned = 0;
     const void* naive = nullptr;
@@ -303,6 +312,54 @@ static stencil_status_t configure_tc(stencil_plan* p) {
     return configure_umma(p);
 }
 
+// The cluster-resident kernel holds the grid in the shared memory of one
+// cluster of C <= 16 CTAs and runs a whole run in one launch.  It applies when
+// some C in {1, 2, 4, 8, 16} gives slabs that fit a CTA's shared memory and
+// are at least R rows high (periodic grids also need nx >= R), and the
+// cluster can be scheduled.  Sets p->res_ok (bit log2 C per usable C) and
+// returns the largest usable C, or 0.
+static int resident_candidates(stencil_plan* p) {
+    p->res_ok = 0;
+    if (p->compute != STENCIL_COMPUTE_FP32) return 0;
+    const int periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+    if (periodic && p->nx < p->R) return 0;
+    if (p->ny > (1 << 20) || p->nx > (1 << 20)) return 0;
+    const void* fn = get_resident_kernel(p->R, p->star, p->dtype);
+    if (!fn) return 0;
+    int max_smem = 0;
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int best = 0;
+    for (int C = 1; C <= resident_max_cluster(); C *= 2) {
+        int rp = 0;
+        const int smem = resident_smem_bytes((int)p->ny, (int)p->nx, p->R, periodic, C, &rp);
+        if (smem < 0 || smem > max_smem) continue;
+        if (!resident_cluster_fits(fn, C, smem)) continue;
+        int lg = 0;
+        while ((1 << lg) < C) ++lg;
+        p->res_ok |= 1 << lg;
+        best = C;
+    }
+    p->res_fn = fn;
+    return best;
+}
+
+static stencil_status_t use_resident(stencil_plan* p, int C) {
+    const int periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+    int rp = 0;
+    const int smem = resident_smem_bytes((int)p->ny, (int)p->nx, p->R, periodic, C, &rp);
+    if (smem < 0) return fail(STENCIL_ERR_UNSUPPORTED, "grid does not fit the cluster-resident kernel");
+    CK(cudaFuncSetAttribute(p->res_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (C > 8) CK(cudaFuncSetAttribute(p->res_fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    p->kernel = STENCIL_KERNEL_RESIDENT;
+    p->res_c = C;
+    p->res_rp = rp;
+    p->res_smem = smem;
+    return STENCIL_OK;
+}
+
 static stencil_status_t configure_naive(stencil_plan* p) {
     p->naive = get_naive_kernel(p->R, p->dtype);
     if (!p->naive) return fail(STENCIL_ERR_UNSUPPORTED, "no naive kernel for this radius");
@@ -355,6 +412,21 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
         }
         return STENCIL_OK;
     }
+    if (p->kernel == STENCIL_KERNEL_RESIDENT) {
+        ResidentParams rp{};
+        rp.in = src;
+        rp.out = dst;
+        rp.ny = (int)p->ny;
+        rp.nx = (int)p->nx;
+        rp.ld = (int)p->nx;
+        rp.T = nlev;
+        rp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+        rp.rp = p->res_rp;
+        rp.pitch = (int)p->nx + 2 * p->R;
+        rp.w = p->w;
+        CK(launch_resident(p->res_fn, p->res_c, p->res_smem, rp, st));
+        return STENCIL_OK;
+    }
     if (p->kernel == STENCIL_KERNEL_NAIVE) {
         dim3 block(32, 8), grid((unsigned)p->strips, (unsigned)p->tiles_y);
         long long ny = p->ny, nx = p->nx;
@@ -394,6 +466,10 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
 // split greedily into instantiated depths.
 static std::vector<int> launch_depths(const stencil_plan* p, int64_t T) {
     std::vector<int> d;
+    if (p->kernel == STENCIL_KERNEL_RESIDENT) {  // the whole run in one launch (chunks of 2^30 steps)
+        for (int64_t t = 0; t < T; t += (1 << 30)) d.push_back((int)std::min<int64_t>(T - t, 1 << 30));
+        return d;
+    }
     const int k = p->kernel == STENCIL_KERNEL_STREAM ? p->k : 1;
     for (int64_t t = 0; t < T / k; ++t) d.push_back(k);
     int rem = (int)(T % k);
@@ -526,6 +602,65 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
     return STENCIL_OK;
 }
 
+// Small grids (plans that chose the cluster-resident kernel): time that kernel
+// at every usable cluster size (runs of 64 steps from `in` into the workspace)
+// and the autotuned streaming kernel, per step, and keep the faster.  The
+// decision is cached like the streaming kernel's.
+static std::map<TuneKey, int> g_res_tune_cache;  // cluster size, or 0 for the streaming kernel
+
+static stencil_status_t autotune_resident(stencil_plan* p, const void* in, cudaStream_t st) {
+    const TuneKey key(p->ny, p->nx, p->R, p->star, p->dtype, p->boundary, p->device);
+    int decision = -1;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_res_tune_cache.find(key);
+        if (it != g_res_tune_cache.end()) decision = it->second;
+    }
+    if (decision < 0) {
+        constexpr int S = 64;
+        const int reps = (int)std::max(2.0, std::min(16.0, 1e8 / ((double)p->ny * (double)p->nx * S)));
+        float best = 1e30f;
+        decision = 0;
+        for (int lg = 0; (1 << lg) <= resident_max_cluster(); ++lg) {
+            if (!((p->res_ok >> lg) & 1)) continue;
+            stencil_status_t s = use_resident(p, 1 << lg);
+            if (s != STENCIL_OK) return s;
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            s = launch_once(p, in, p->ws, S, st);  // warm-up
+            if (s == STENCIL_OK) {
+                cudaEventRecord(e0, st);
+                for (int i = 0; i < reps && s == STENCIL_OK; ++i) s = launch_once(p, in, p->ws, S, st);
+                cudaEventRecord(e1, st);
+            }
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (s == STENCIL_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (s != STENCIL_OK) return s;
+            if (e != cudaSuccess) return fail(STENCIL_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+            const float per_step = ms / (float)(reps * S);
+            if (per_step < best) {
+                best = per_step;
+                decision = 1 << lg;
+            }
+        }
+        stencil_status_t s = autotune(p, in, st);  // configures the best streaming kernel
+        if (s != STENCIL_OK) return s;
+        const int sreps = (int)std::max(2.0, std::min(64.0, 1e8 / ((double)p->ny * (double)p->nx * p->k)));
+        float ms = 0.f;
+        s = time_launch(p, in, sreps, st, &ms);
+        if (s != STENCIL_OK) return s;
+        if (ms / (float)(sreps * p->k) < best) decision = 0;
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_res_tune_cache[key] = decision;
+    }
+    if (decision > 0) return use_resident(p, decision);
+    return autotune(p, in, st);
+}
+
 extern "C" {
 
 const char* stencil_status_string(stencil_status_t s) {
@@ -562,7 +697,7 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     stencil_options_t o{};
     if (opt) o = *opt;
     if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_3XTF32 || o.kernel < 0 ||
-        o.kernel > STENCIL_KERNEL_TC_UMMA || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0 ||
+        o.kernel > STENCIL_KERNEL_RESIDENT || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0 ||
         o.mma_n < 0)
         return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
 
@@ -608,7 +743,9 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     }
 
     stencil_status_t st;
-    if (p->compute != STENCIL_COMPUTE_FP32 || o.kernel >= STENCIL_KERNEL_TC) {
+    const bool tc_kernel = o.kernel == STENCIL_KERNEL_TC || o.kernel == STENCIL_KERNEL_TC_WARP ||
+                           o.kernel == STENCIL_KERNEL_TC_UMMA;
+    if (p->compute != STENCIL_COMPUTE_FP32 || tc_kernel) {
         if (p->compute == STENCIL_COMPUTE_FP32) p->compute = STENCIL_COMPUTE_TC_TF32;
         st = configure_tc(p);
     } else if (o.kernel == STENCIL_KERNEL_NAIVE) {
@@ -617,6 +754,17 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
         const int k = o.tb_depth > 0 ? o.tb_depth : default_depth(radius, star);
         const int threads = o.threads > 0 ? o.threads : kDefaultThreads;
         st = configure_stream(p, std::min(k, stream_kmax(radius, star)), threads, o.tile_rows);
+        // Small grids: the cluster-resident kernel, unless the caller asked for
+        // the streaming kernel or set one of its options.
+        const bool stream_opts = o.tb_depth > 0 || o.threads > 0 || o.tile_rows > 0;
+        if (st == STENCIL_OK && (o.kernel == STENCIL_KERNEL_RESIDENT ||
+                                 (o.kernel == STENCIL_KERNEL_AUTO && !stream_opts))) {
+            const int C = resident_candidates(p);
+            if (C > 0)
+                st = use_resident(p, C);
+            else if (o.kernel == STENCIL_KERNEL_RESIDENT)
+                st = fail(STENCIL_ERR_UNSUPPORTED, "grid too large for the cluster-resident kernel");
+        }
     }
     if (st != STENCIL_OK) return bail(st);
 
@@ -670,6 +818,15 @@ stencil_status_t stencil_plan_info(const stencil_plan_t* p, stencil_plan_info_t*
     i.smem_bytes = p->smem;
     i.workspace_bytes = (int64_t)((size_t)p->ny * p->nx * p->elem);
     i.mma_n = p->umma_n;
+    if (p->kernel == STENCIL_KERNEL_RESIDENT) {
+        i.tb_depth = 0;  // every step of a run in one launch
+        i.threads = resident_threads();
+        i.halo_cols = p->R;
+        i.tile_cols = (int)p->nx;
+        i.tile_rows = p->res_rp;
+        i.ctas = p->res_c;
+        i.smem_bytes = p->res_smem;
+    }
     if (p->umma_n) {
         i.threads = box49_umma_threads();
         i.ctas = p->umma_ctas;
@@ -698,6 +855,11 @@ stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64
         if (s != STENCIL_OK) return s;
         p->tuned = 1;
     }
+    if (p->opt.autotune && !p->tuned && p->kernel == STENCIL_KERNEL_RESIDENT && T > 0) {
+        stencil_status_t s = autotune_resident(p, in, st);
+        if (s != STENCIL_OK) return s;
+        p->tuned = 1;
+    }
     if (p->opt.autotune && !p->tuned && p->kernel == STENCIL_KERNEL_STREAM && T > 0) {
         stencil_status_t s = autotune(p, in, st);
         if (s != STENCIL_OK) return s;
@@ -709,6 +871,15 @@ stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64
     }
     std::vector<int> depths = launch_depths(p, T);
     const void* src = in;
+    if (p->kernel == STENCIL_KERNEL_RESIDENT) {
+        // one launch reads all of its input before it writes any output
+        for (size_t i = 0; i < depths.size(); ++i) {
+            stencil_status_t s = launch_once(p, src, out, depths[i], st);
+            if (s != STENCIL_OK) return s;
+            src = out;
+        }
+        return STENCIL_OK;
+    }
     if (in == out && depths.size() % 2 == 1) {
         // An odd launch count would make launch 1 write the grid it reads.
         // Split one launch in two when possible, else stage the input.
