@@ -131,17 +131,25 @@ def _barrier(world):
         import torch
         import torch.distributed as dist
         dist.barrier()
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
 
 
 def _max_over_ranks(world, x: float) -> float:
+    """The slowest rank's time: whole-job throughput divides by it."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, max_ms: float) -> float:
+    """GStencil/s of N independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3) / 1e9
 
 
 def cpu_oracle_sample(steps_per_pattern: int = 40, n: int = N):
@@ -273,12 +281,12 @@ def run_variant(args, world, rank, local):
         e2e_ms = _time_steps(e2e_step, max(1, min(args.steps, 3)), 1, stream)
         nbytes = sum(h.numel() * 4 for h in host_in)
         line.update({
-            "metric": "GStencil/s (FP32 batched: 256 grids, 200 steps)", "value": world * units / (ms * 1e-3) / 1e9,
+            "metric": "GStencil/s (FP32 batched: 256 grids, 200 steps)", "value": whole_job_rate(world, units, ms),
             "unit": "GStencil/s", "ms_per_step": ms, "dtype": "f32",
             "config": {"workload": VARIANTS[name], "grids": 256, "points": int(sum(int(s) ** 2 for s in sides)),
                        "T": 200, "batch": info, "l2": "inputs larger than L2 (152.6 M points, 610 MB per copy)"},
             "gpu_launches": info["launches"] * args.steps,
-            "e2e": {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GStencil/s",
+            "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "api": "stencil_run_batched with torch copies of pinned host grids"},
             "clocks": clocks,
@@ -329,7 +337,7 @@ def run_variant(args, world, rank, local):
         alg_bytes = 2.0 * esz * n * n * k
         line.update({
             "metric": f"GStencil/s ({name}: {', '.join(pats)}, {n}^2, {T} steps)",
-            "value": world * units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
+            "value": whole_job_rate(world, units, ms), "unit": "GStencil/s", "ms_per_step": ms,
             "dtype": dtype,
             "config": {"workload": VARIANTS[name], "ny": n, "nx": n, "T": T, "compute": compute,
                        "tc_engine": args.tc_engine if compute.startswith("tc") else None,
@@ -345,7 +353,7 @@ def run_variant(args, world, rank, local):
                                        "traffic": _ncu_traffic(
                                            f"box49_{'umma' if info0['kernel'] == 5 else 'warp'}_{dtype}_{n}")
                                        if compute.startswith("tc") else None},
-            "e2e": {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GStencil/s",
+            "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
                     "h2d_bytes_per_step": len(pats) * n * n * esz, "d2h_bytes_per_step": len(pats) * n * n * esz,
                     "api": "Plan.run (stencil_run) with torch copies of pinned host grids"},
             "clocks": clocks,
@@ -385,7 +393,7 @@ def run_variant(args, world, rank, local):
         line.update({
             "metric": "GStencil/s (weak-scaling sweep: 4 patterns x 128^2..32768^2 + Star-2D5P 44800^2, "
                       "1000 steps each)",
-            "value": world * total_units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
+            "value": whole_job_rate(world, total_units, ms), "unit": "GStencil/s", "ms_per_step": ms,
             "dtype": "f32",
             "config": {"workload": VARIANTS[name], "T": T, "table": table,
                        "l2": "grids up to 4096^2 fit in L2 (launch- and latency-bound); larger ones stream "
@@ -435,14 +443,14 @@ def run_variant(args, world, rank, local):
         units = float(n) * n * T
         line.update({
             "metric": "GStencil/s (Heat-2D FP32 forward + adjoint, 4096^2, 512 steps)",
-            "value": world * units / (ms * 1e-3) / 1e9, "unit": "GStencil/s", "ms_per_step": ms,
+            "value": whole_job_rate(world, units, ms), "unit": "GStencil/s", "ms_per_step": ms,
             "dtype": "f32",
             "config": {"workload": VARIANTS[name], "ny": n, "nx": n, "T": T,
                        "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
                        "ckpt_interval": int(np.ceil(np.sqrt(T))), "plan": plan.info(),
                        "l2": "inputs larger than L2 (64 MiB per grid, 23 checkpoints)"},
             "gpu_launches": launches * args.steps,
-            "e2e": {"value": world * units / (e2e_ms * 1e-3) / 1e9, "unit": "GStencil/s",
+            "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
                     "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4 + 9 * 8,
                     "api": "Plan.run + stencil_adjoint (torch copies of pinned host u0/target, "
                            "gradients read back)"},
@@ -542,7 +550,7 @@ def main():
 
     updates_per_step = len(PATTERNS) * N * N * T
     ms_per_step = ms_total / args.steps
-    value = world * updates_per_step / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_rate(world, updates_per_step, ms_per_step)
 
     # Roofline of the dominant kernel (the pattern with the larger share of the step).
     peaks, peak_src = _peaks()
