@@ -101,8 +101,10 @@ typedef enum {
  * cluster (two FP32 copies in the shared memory of at most 16 CTAs; roughly up
  * to 700 x 700 for radius 1) and no streaming-kernel option (tb_depth,
  * threads, tile_rows) is set; otherwise STREAM.  With autotune the first run
- * times both.  stencil_plan_info reports tb_depth = 0 for RESIDENT (one
- * launch per run), ctas = the cluster size and tile_rows = the slab height. */
+ * times both (and, for RESIDENT, every cluster size and blocking depth).  With
+ * kernel = RESIDENT, tb_depth sets its steps per halo exchange (default 1).
+ * stencil_plan_info reports tb_depth = 0 for RESIDENT (one launch per run),
+ * ctas = the cluster size and tile_rows = the slab height. */
 typedef struct {
     int compute;      /* stencil_compute_t                                          */
     int kernel;       /* stencil_kernel_t                                           */

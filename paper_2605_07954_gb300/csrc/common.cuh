@@ -52,6 +52,8 @@ struct ResidentParams {
     int periodic;  // 1: wrap; 0: zero outside the grid
     int rp;        // slab rows per CTA
     int pitch;     // floats per staged row (nx + 2R)
+    int kb;        // steps per halo exchange (temporal blocking depth)
+    int H;         // staged halo rows on each side (kb * R)
     Weights w;
 };
 

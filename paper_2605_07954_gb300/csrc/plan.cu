@@ -42,7 +42,7 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
 const void* get_resident_kernel(int radius, int star, int dtype);
 int resident_threads();
 int resident_max_cluster();
-int resident_smem_bytes(int ny, int nx, int radius, int periodic, int C, int* rp_out);
+int resident_config(int ny, int nx, int radius, int periodic, int C, int kb, int max_smem, int* rp_out);
 cudaError_t launch_resident(const void* fn, int C, int smem, const ResidentParams& prm, cudaStream_t st);
 bool resident_cluster_fits(const void* fn, int C, int smem);
 struct TcParams {  // must match box49_tc.cu
@@ -94,7 +94,7 @@ struct stencil_plan {
     int umma_ctas = 0;
     // cluster-resident kernel (sweep_resident.cu): usable cluster sizes (bit log2 C), the one in use
     const void* res_fn = nullptr;
-    int res_ok = 0, res_c = 0, res_rp = 0, res_smem = 0;
+    int res_ok = 0, res_c = 0, res_rp = 0, res_kb = 1, res_smem = 0, res_max_smem = 0;
     unsigned smem_set = 0;  // bit 2k+vec: that kernel's shared-memory attribute is set
     int tuned = 0;
     const void* naive = nullptr;
@@ -318,7 +318,7 @@ static stencil_status_t configure_tc(stencil_plan* p) {
 // are at least R rows high (periodic grids also need nx >= R), and the
 // cluster can be scheduled.  Sets p->res_ok (bit log2 C per usable C) and
 // returns the largest usable C, or 0.
-static int resident_candidates(stencil_plan* p) {
+static int resident_candidates(stencil_plan* p, int kb = 1) {
     p->res_ok = 0;
     if (p->compute != STENCIL_COMPUTE_FP32) return 0;
     const int periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
@@ -331,11 +331,12 @@ static int resident_candidates(stencil_plan* p) {
         cudaGetLastError();
         return 0;
     }
+    p->res_max_smem = max_smem;
     int best = 0;
     for (int C = 1; C <= resident_max_cluster(); C *= 2) {
         int rp = 0;
-        const int smem = resident_smem_bytes((int)p->ny, (int)p->nx, p->R, periodic, C, &rp);
-        if (smem < 0 || smem > max_smem) continue;
+        const int smem = resident_config((int)p->ny, (int)p->nx, p->R, periodic, C, kb, max_smem, &rp);
+        if (smem < 0) continue;
         if (!resident_cluster_fits(fn, C, smem)) continue;
         int lg = 0;
         while ((1 << lg) < C) ++lg;
@@ -346,16 +347,20 @@ static int resident_candidates(stencil_plan* p) {
     return best;
 }
 
-static stencil_status_t use_resident(stencil_plan* p, int C) {
+// Switch the plan to the resident kernel with cluster size C and kb steps per
+// halo exchange (kb = 1 by default: deeper blocking only pays where a step's
+// work is small next to the cluster barrier, which autotuning measures).
+static stencil_status_t use_resident(stencil_plan* p, int C, int kb = 1) {
     const int periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
     int rp = 0;
-    const int smem = resident_smem_bytes((int)p->ny, (int)p->nx, p->R, periodic, C, &rp);
+    const int smem = resident_config((int)p->ny, (int)p->nx, p->R, periodic, C, kb, p->res_max_smem, &rp);
     if (smem < 0) return fail(STENCIL_ERR_UNSUPPORTED, "grid does not fit the cluster-resident kernel");
     CK(cudaFuncSetAttribute(p->res_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     if (C > 8) CK(cudaFuncSetAttribute(p->res_fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     p->kernel = STENCIL_KERNEL_RESIDENT;
     p->res_c = C;
     p->res_rp = rp;
+    p->res_kb = kb;
     p->res_smem = smem;
     return STENCIL_OK;
 }
@@ -423,6 +428,8 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
         rp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
         rp.rp = p->res_rp;
         rp.pitch = (int)p->nx + 2 * p->R;
+        rp.kb = p->res_kb;
+        rp.H = p->res_kb * p->R;
         rp.w = p->w;
         CK(launch_resident(p->res_fn, p->res_c, p->res_smem, rp, st));
         return STENCIL_OK;
@@ -606,7 +613,7 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
 // at every usable cluster size (runs of 64 steps from `in` into the workspace)
 // and the autotuned streaming kernel, per step, and keep the faster.  The
 // decision is cached like the streaming kernel's.
-static std::map<TuneKey, int> g_res_tune_cache;  // cluster size, or 0 for the streaming kernel
+static std::map<TuneKey, int> g_res_tune_cache;  // 16 * kb + log2(C) + 1, or 0 for the streaming kernel
 
 static stencil_status_t autotune_resident(stencil_plan* p, const void* in, cudaStream_t st) {
     const TuneKey key(p->ny, p->nx, p->R, p->star, p->dtype, p->boundary, p->device);
@@ -623,28 +630,34 @@ static stencil_status_t autotune_resident(stencil_plan* p, const void* in, cudaS
         decision = 0;
         for (int lg = 0; (1 << lg) <= resident_max_cluster(); ++lg) {
             if (!((p->res_ok >> lg) & 1)) continue;
-            stencil_status_t s = use_resident(p, 1 << lg);
-            if (s != STENCIL_OK) return s;
-            cudaEvent_t e0, e1;
-            CK(cudaEventCreate(&e0));
-            CK(cudaEventCreate(&e1));
-            s = launch_once(p, in, p->ws, S, st);  // warm-up
-            if (s == STENCIL_OK) {
-                cudaEventRecord(e0, st);
-                for (int i = 0; i < reps && s == STENCIL_OK; ++i) s = launch_once(p, in, p->ws, S, st);
-                cudaEventRecord(e1, st);
-            }
-            cudaError_t e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (s == STENCIL_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            if (s != STENCIL_OK) return s;
-            if (e != cudaSuccess) return fail(STENCIL_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
-            const float per_step = ms / (float)(reps * S);
-            if (per_step < best) {
-                best = per_step;
-                decision = 1 << lg;
+            for (int kb = 1; kb <= 8; kb *= 2) {
+                int rp = 0;
+                const int periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+                if (resident_config((int)p->ny, (int)p->nx, p->R, periodic, 1 << lg, kb, p->res_max_smem, &rp) < 0)
+                    continue;
+                stencil_status_t s = use_resident(p, 1 << lg, kb);
+                if (s != STENCIL_OK) return s;
+                cudaEvent_t e0, e1;
+                CK(cudaEventCreate(&e0));
+                CK(cudaEventCreate(&e1));
+                s = launch_once(p, in, p->ws, S, st);  // warm-up
+                if (s == STENCIL_OK) {
+                    cudaEventRecord(e0, st);
+                    for (int i = 0; i < reps && s == STENCIL_OK; ++i) s = launch_once(p, in, p->ws, S, st);
+                    cudaEventRecord(e1, st);
+                }
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (s == STENCIL_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (s != STENCIL_OK) return s;
+                if (e != cudaSuccess) return fail(STENCIL_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+                const float per_step = ms / (float)(reps * S);
+                if (per_step < best) {
+                    best = per_step;
+                    decision = 16 * kb + lg + 1;
+                }
             }
         }
         stencil_status_t s = autotune(p, in, st);  // configures the best streaming kernel
@@ -657,7 +670,7 @@ static stencil_status_t autotune_resident(stencil_plan* p, const void* in, cudaS
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_res_tune_cache[key] = decision;
     }
-    if (decision > 0) return use_resident(p, decision);
+    if (decision > 0) return use_resident(p, 1 << ((decision & 15) - 1), decision >> 4);
     return autotune(p, in, st);
 }
 
@@ -756,14 +769,16 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
         st = configure_stream(p, std::min(k, stream_kmax(radius, star)), threads, o.tile_rows);
         // Small grids: the cluster-resident kernel, unless the caller asked for
         // the streaming kernel or set one of its options.
+        // With kernel = RESIDENT, tb_depth is its number of steps per halo exchange.
         const bool stream_opts = o.tb_depth > 0 || o.threads > 0 || o.tile_rows > 0;
         if (st == STENCIL_OK && (o.kernel == STENCIL_KERNEL_RESIDENT ||
                                  (o.kernel == STENCIL_KERNEL_AUTO && !stream_opts))) {
-            const int C = resident_candidates(p);
+            const int kb = (o.kernel == STENCIL_KERNEL_RESIDENT && o.tb_depth > 0) ? o.tb_depth : 1;
+            const int C = resident_candidates(p, kb);
             if (C > 0)
-                st = use_resident(p, C);
+                st = use_resident(p, C, kb);
             else if (o.kernel == STENCIL_KERNEL_RESIDENT)
-                st = fail(STENCIL_ERR_UNSUPPORTED, "grid too large for the cluster-resident kernel");
+                st = fail(STENCIL_ERR_UNSUPPORTED, "grid too large for the cluster-resident kernel at this depth");
         }
     }
     if (st != STENCIL_OK) return bail(st);

@@ -143,3 +143,23 @@ def test_rejects_grids_that_do_not_fit():
     from paper_2605_07954_gb300 import Plan, StencilError
     with pytest.raises(StencilError, match="UNSUPPORTED"):
         Plan(2048, 2048, inputs.pattern_weights("box9"), kernel="resident")
+
+
+@pytest.mark.parametrize("name,kb", [("heat5", 2), ("box9", 4), ("box9", 8), ("star13", 2), ("box25", 2)])
+@pytest.mark.parametrize("boundary", ["zero", "periodic"])
+def test_blocked_exchange_depths(oracle, name, kb, boundary):
+    """kb steps per halo exchange (slabs with kb*R-deep halos, redundant rows
+    recomputed, double-buffered mailboxes): the same results, for step counts
+    that are and are not multiples of kb."""
+    W = _weights(name)
+    u0 = inputs.field(260, 300)
+    for T in (kb * 3, kb * 3 + 1):
+        got, info, launches = _run(u0, W, T, boundary, kernel="resident", tb_depth=kb)
+        assert info["kernel"] == 6 and launches == 1
+        ref = oracle.sweep_f64(u0, W, T, boundary)
+        assert rel_l2(got, ref) <= fp32_tol(T)
+        assert rel_linf(got, ref) <= fp32_elem_tol(T, int(np.count_nonzero(W)))
+    # bit-identical to one step per exchange: the per-point arithmetic is the same
+    a, _, _ = _run(u0, W, 3 * kb + 1, boundary, kernel="resident", tb_depth=kb)
+    b, _, _ = _run(u0, W, 3 * kb + 1, boundary, kernel="resident")
+    assert np.array_equal(a, b)
