@@ -486,6 +486,8 @@ def main():
                     help="comma-separated subset of box9,star13 (profiling captures)")
     ap.add_argument("--workload", default="box9+star13", choices=sorted(VARIANTS) + ["box9+star13"],
                     help="box9+star13 (the headline) or one of the variant workloads")
+    ap.add_argument("--tb-depth", type=int, default=0,
+                    help="headline workload: fixed temporal-blocking depth (profiling captures)")
     ap.add_argument("--tc-engine", default="auto", choices=["auto", "warp", "umma"],
                     help="tensor-core workloads: autotuned engine choice, warp-level MMAs, or tcgen05")
     args = ap.parse_args()
@@ -508,7 +510,7 @@ def main():
     plans, xs, outs = {}, {}, {}
     for p in PATTERNS:
         W = inputs.pattern_weights(p)
-        plans[p] = Plan(N, N, W, autotune=not args.no_autotune)
+        plans[p] = Plan(N, N, W, tb_depth=args.tb_depth, autotune=not args.no_autotune)
         xs[p] = torch.from_numpy(inputs.field(N, N)).cuda()
         outs[p] = torch.empty_like(xs[p])
     stream = torch.cuda.current_stream()
