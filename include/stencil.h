@@ -113,6 +113,10 @@ typedef struct {
     int tile_rows;    /* output rows per CTA tile of the streaming kernel           */
     int autotune;     /* 1: time candidate configurations on first run              */
     int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16)      */
+    int timeout_ms;   /* tcgen05 engine: limit of each device-side wait (0 = 2000)  */
+    int debug_withhold; /* test hook, 0 in normal use: 1 makes CTA 0 of the tcgen05
+                           engine withhold its first accumulator-ready signal, so its
+                           epilogue wait runs out and the run reports TIMEOUT         */
 } stencil_options_t;
 
 /* What a plan decided.  Filled by stencil_plan_info(). */

@@ -36,7 +36,8 @@ class Plan:
 
     def __init__(self, ny: int, nx: int, weights, dtype: str = "f32", boundary: str = "zero",
                  compute: str = "auto", kernel: str = "auto", tb_depth: int = 0,
-                 threads: int = 0, tile_rows: int = 0, autotune: bool = False, mma_n: int = 0):
+                 threads: int = 0, tile_rows: int = 0, autotune: bool = False, mma_n: int = 0,
+                 timeout_ms: int = 0, debug_withhold: int = 0):
         lib = _capi.load()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
         d = w.shape[0]
@@ -47,7 +48,8 @@ class Plan:
         self.dtype = dtype
         self.weights = w
         opt = _capi.stencil_options_t(COMPUTES[compute], KERNELS[kernel], int(tb_depth),
-                                      int(threads), int(tile_rows), int(bool(autotune)), int(mma_n))
+                                      int(threads), int(tile_rows), int(bool(autotune)), int(mma_n),
+                                      int(timeout_ms), int(debug_withhold))
         h = ctypes.c_void_p()
         check(lib.stencil_plan_create(ctypes.byref(h), int(ny), int(nx), self.radius,
                                       w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),

@@ -29,7 +29,7 @@ STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_STREAM = 0, 1, 2
 class stencil_options_t(ctypes.Structure):
     _fields_ = [("compute", ctypes.c_int), ("kernel", ctypes.c_int), ("tb_depth", ctypes.c_int),
                 ("threads", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("mma_n", ctypes.c_int)]
+                ("mma_n", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("debug_withhold", ctypes.c_int)]
 
 
 class stencil_plan_info_t(ctypes.Structure):

@@ -43,7 +43,7 @@
 // per cycle, so the widest N (fewest re-reads of the row-shifted A) is the
 // fastest: N = 64 gives 912 GStencil/s.  mbarriers: full / empty per stage, tmem_full /
 // tmem_empty per accumulator, one drain barrier.  Every wait is bounded
-// (%globaltimer, 2 s, and an iteration cap): when one expires the kernel
+// (%globaltimer, 2 s by default, and an iteration cap): when one expires the kernel
 // stores STENCIL_ERR_TIMEOUT in the status word, raises a CTA-wide abort flag,
 // waits (again bounded) for its own TMA loads and MMAs in flight, frees its
 // tensor memory and returns.
@@ -111,6 +111,8 @@ struct UmParams {
     int tiles_x, tiles;
     int round_out;      // TF32: store TF32-rounded values
     unsigned* status;   // STENCIL_ERR_TIMEOUT on an expired wait
+    long long wait_ns;  // limit of each mbarrier wait
+    int withhold;       // test hook: CTA 0 withholds its first accumulator-ready signal
     float w[49];
 };
 
@@ -150,18 +152,17 @@ __device__ __forceinline__ bool um_bar_try(unsigned bar, unsigned parity) {
     return ok != 0;
 }
 
-constexpr long long kUmWaitNs = 2000000000LL;
 constexpr unsigned kUmWaitIters = 1u << 26;
 
 // Wait for the phase of `parity` of `bar`.  Gives up when the CTA's abort flag
-// is raised, or after ~2 s (then records a timeout and raises the flag).
+// is raised, or after `limit_ns` (then records a timeout and raises the flag).
 __device__ __forceinline__ bool um_wait(unsigned bar, unsigned parity, volatile int* abort_flag,
-                                        unsigned* status) {
+                                        unsigned* status, long long limit_ns) {
     const long long t0 = um_now();
     for (unsigned it = 0;; ++it) {
         if (um_bar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if ((it & 63u) == 63u && (um_now() - t0 > kUmWaitNs || it > kUmWaitIters)) {
+        if ((it & 63u) == 63u && (um_now() - t0 > limit_ns || it > kUmWaitIters)) {
             atomicCAS(status, 0u, (unsigned)STENCIL_ERR_TIMEOUT);
             *abort_flag = 1;
             return false;
@@ -170,11 +171,11 @@ __device__ __forceinline__ bool um_wait(unsigned bar, unsigned parity, volatile 
 }
 
 // Bounded wait used while winding down (ignores the abort flag).
-__device__ __forceinline__ void um_drain(unsigned bar, unsigned parity, unsigned* status) {
+__device__ __forceinline__ void um_drain(unsigned bar, unsigned parity, unsigned* status, long long limit_ns) {
     const long long t0 = um_now();
     for (unsigned it = 0;; ++it) {
         if (um_bar_try(bar, parity)) return;
-        if ((it & 63u) == 63u && (um_now() - t0 > kUmWaitNs || it > kUmWaitIters)) {
+        if ((it & 63u) == 63u && (um_now() - t0 > limit_ns || it > kUmWaitIters)) {
             atomicCAS(status, 0u, (unsigned)STENCIL_ERR_TIMEOUT);
             return;
         }
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(kUmThreads, 1)
         for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, ++it) {
             const int s = it % C::STAGES;
             int ok = 1;
-            if (lane == 0) ok = um_wait(empty0 + 8u * s, ((it / C::STAGES) & 1) ^ 1, &s_abort, p.status);
+            if (lane == 0) ok = um_wait(empty0 + 8u * s, ((it / C::STAGES) & 1) ^ 1, &s_abort, p.status, p.wait_ns);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             if (lane == 0) {
                 const int x0 = (tile % p.tiles_x) * kUmCols, y0 = (tile / p.tiles_x) * kUmRows;
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(kUmThreads, 1)
         // Loads still in flight (only after an abort) land before the CTA exits.
         if (lane == 0) {
             for (int i = it - C::STAGES < 0 ? 0 : it - C::STAGES; i < it; ++i)
-                um_drain(full0 + 8u * (i % C::STAGES), (i / C::STAGES) & 1, p.status);
+                um_drain(full0 + 8u * (i % C::STAGES), (i / C::STAGES) & 1, p.status, p.wait_ns);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -400,8 +401,8 @@ __global__ void __launch_bounds__(kUmThreads, 1)
             const int s = it % C::STAGES, b = it & 1;
             int ok = 1;
             if (lane == 0) {
-                ok = um_wait(full0 + 8u * s, (it / C::STAGES) & 1, &s_abort, p.status) &&
-                     um_wait(tempty0 + 8u * b, ((it >> 1) & 1) ^ 1, &s_abort, p.status);
+                ok = um_wait(full0 + 8u * s, (it / C::STAGES) & 1, &s_abort, p.status, p.wait_ns) &&
+                     um_wait(tempty0 + 8u * b, ((it >> 1) & 1) ^ 1, &s_abort, p.status, p.wait_ns);
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             um_fence_after();
@@ -430,7 +431,8 @@ __global__ void __launch_bounds__(kUmThreads, 1)
                     }
                 }
                 um_commit(empty0 + 8u * s);  // the stage is free once these MMAs have read it
-                um_commit(tfull0 + 8u * b);  // the accumulator is complete
+                if (!(p.withhold && blockIdx.x == 0 && it == 0))
+                    um_commit(tfull0 + 8u * b);  // the accumulator is complete
                 issued = 1;
             }
             __syncwarp();
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kUmThreads, 1)
         // Every MMA issued is complete before the tensor memory is released.
         if (lane == 0 && issued) {
             um_commit(drain);
-            um_drain(drain, 0, p.status);
+            um_drain(drain, 0, p.status, p.wait_ns);
         }
         __syncwarp();
     } else {
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kUmThreads, 1)
         for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, ++it) {
             const int b = it & 1;
             int ok = 1;
-            if (lane == 0) ok = um_wait(tfull0 + 8u * b, (it >> 1) & 1, &s_abort, p.status);
+            if (lane == 0) ok = um_wait(tfull0 + 8u * b, (it >> 1) & 1, &s_abort, p.status, p.wait_ns);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!um_epi_and(ok)) break;  // the four epilogue warps leave together
             um_fence_after();
@@ -579,7 +581,8 @@ static CUresult um_encode(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* ma
 // bytes, ny >= 134 and nx >= 128.  Returns cudaErrorNotSupported when no
 // tensor map can be made for this layout.
 cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int ny, int nx, int ld,
-                              int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st) {
+                              int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st,
+                              int timeout_ms, int withhold) {
     const void* fn = get_box49_umma_kernel(tf32, nt);
     PFN_cuTensorMapEncodeTiled_v12000 enc = um_encoder();
     if (!fn || !enc) return cudaErrorNotSupported;
@@ -599,6 +602,8 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
     up.tiles = up.tiles_x * ((ny + kUmRows - 1) / kUmRows);
     up.round_out = round_out;
     up.status = status;
+    up.wait_ns = (long long)(timeout_ms > 0 ? timeout_ms : 2000) * 1000000LL;
+    up.withhold = withhold;
     for (int i = 0; i < 49; ++i) up.w[i] = w[i];
     void* args[] = {&map_sw, &map_pl, &map_out, &up};
     const int grid = ctas < up.tiles ? ctas : up.tiles;

@@ -38,7 +38,8 @@ const void* get_box49_umma_kernel(int tf32, int nt);
 int box49_umma_smem_bytes(int tf32, int nt);
 int box49_umma_threads();
 cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int ny, int nx, int ld,
-                              int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st);
+                              int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st,
+                              int timeout_ms, int withhold);
 const void* get_resident_kernel(int radius, int star, int dtype);
 int resident_threads();
 int resident_max_cluster();
@@ -403,7 +404,8 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
         const int tf32 = p->compute == STENCIL_COMPUTE_TC_TF32;
         if (p->umma_n && !(tf32 && first) && (uintptr_t)src % 16 == 0 && (uintptr_t)dst % 16 == 0) {
             const cudaError_t e = launch_box49_umma(tf32, p->umma_n, src, dst, tp.ny, tp.nx, tp.ld,
-                                                    tf32 && !last, p->status, p->w.w, p->umma_ctas, st);
+                                                    tf32 && !last, p->status, p->w.w, p->umma_ctas, st,
+                                                    p->opt.timeout_ms, p->opt.debug_withhold);
             if (e == cudaSuccess) return STENCIL_OK;
             if (e != cudaErrorNotSupported) CK(e);
             // no tensor map for this layout: the warp-MMA engine takes the step
@@ -711,7 +713,7 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     if (opt) o = *opt;
     if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_3XTF32 || o.kernel < 0 ||
         o.kernel > STENCIL_KERNEL_RESIDENT || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0 ||
-        o.mma_n < 0)
+        o.mma_n < 0 || o.timeout_ms < 0 || o.debug_withhold < 0 || o.debug_withhold > 1)
         return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
 
     stencil_plan* p = new (std::nothrow) stencil_plan();
