@@ -16,6 +16,7 @@ import argparse
 import json
 import os
 import statistics
+import tempfile
 import subprocess
 import sys
 import time
@@ -72,7 +73,8 @@ class ClockSampler:
     def __init__(self, gpu: str):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
