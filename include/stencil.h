@@ -83,8 +83,8 @@ typedef enum {
  * with TC_BF16, FP32 with TC_TF32), rows of a multiple of 16 bytes,
  * ny >= 134 and nx >= 128.  With TC_TF32 the first launch of a run (which rounds the
  * caller's FP32 input to TF32) always runs on the warp-MMA engine.  kernel = TC
- * or AUTO picks tcgen05 for BF16 and the warp engine for TF32 (the faster of
- * each as measured); with autotune the first run times both. */
+ * or AUTO picks tcgen05 where it applies (the faster engine as measured); with
+ * autotune the first run times both. */
 typedef enum {
     STENCIL_KERNEL_AUTO = 0,
     STENCIL_KERNEL_NAIVE = 1,      /* one thread per point, one step per launch      */
@@ -112,7 +112,7 @@ typedef struct {
     int threads;      /* threads per CTA of the streaming kernel (multiple of 32)   */
     int tile_rows;    /* output rows per CTA tile of the streaming kernel           */
     int autotune;     /* 1: time candidate configurations on first run              */
-    int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16)      */
+    int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16/32)   */
     int timeout_ms;   /* tcgen05 engine: limit of each device-side wait (0 = 2000)  */
     int debug_withhold; /* test hook, 0 in normal use: 1 makes CTA 0 of the tcgen05
                            engine withhold its first accumulator-ready signal, so its

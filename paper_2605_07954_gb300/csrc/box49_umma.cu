@@ -38,10 +38,11 @@
 // Two accumulators of 128 TMEM columns let the epilogue of one tile overlap
 // the MMAs of the next; two staging buffers (one where shared memory is
 // short) let the TMA store of one tile overlap the epilogue of the next.
-// Measured on GB300 (16384^2, BF16): the MMAs then cost ~65 cycles each
-// whatever their N, i.e. the A operand streams from shared memory at ~64 B
-// per cycle, so the widest N (fewest re-reads of the row-shifted A) is the
-// fastest: N = 64 gives 912 GStencil/s.  mbarriers: full / empty per stage, tmem_full /
+// Measured on GB300 (16384^2): the MMAs then cost ~65 cycles each whatever
+// their N, i.e. the A operand streams from shared memory at ~64 B per cycle,
+// so the widest N that fits (fewest re-reads of the row-shifted A) is the
+// fastest: BF16 N = 64 916 GStencil/s, TF32 N = 32 492 (its output tile is
+// staged in two column halves to fit).  mbarriers: full / empty per stage, tmem_full /
 // tmem_empty per accumulator, one drain barrier.  Every wait is bounded
 // (%globaltimer, 2 s by default, and an iteration cap): when one expires the kernel
 // stores STENCIL_ERR_TIMEOUT in the status word, raises a CTA-wide abort flag,
@@ -90,16 +91,20 @@ struct UmCfg {
     static constexpr int BPLANE = NT * 16;                       // bytes per B plane
     static constexpr int B_BYTES = BPLANES * BPLANE;
     static constexpr int NBARS = 2 * STAGES + 5;
-    static constexpr int OUT_BYTES = kUmRows * kUmCols * EB;     // one staged output tile
+    static constexpr int OUT_BYTES = kUmRows * kUmCols * EB;     // one output tile
     static constexpr int BASE = STAGES * STAGE_BYTES + 7 * B_BYTES + 8 * NBARS;
-    static constexpr int STG = 1024 + BASE + 2 * OUT_BYTES <= 227 * 1024 ? 2 : 1;  // output staging buffers
-    static constexpr int SMEM = 1024 + BASE + STG * OUT_BYTES;   // + alignment slack
+    // The output tile is staged whole, or in two column halves where shared
+    // memory is short; two staging buffers where they fit.
+    static constexpr int PARTS = 1024 + BASE + OUT_BYTES <= 227 * 1024 ? 1 : 2;
+    static constexpr int PART_BYTES = OUT_BYTES / PARTS;
+    static constexpr int STG = 1024 + BASE + 2 * PART_BYTES <= 227 * 1024 ? 2 : 1;
+    static constexpr int SMEM = 1024 + BASE + STG * PART_BYTES;  // + alignment slack
     static_assert(kUmCols % NT == 0 && NT % 16 == 0, "N-tile width");
     static_assert(kUmCols + KE >= kUmCols + L + 3, "staged columns cover the footprint");
     static_assert((JT - 1) * NT + (KSTEPS - 1) * KE <= kUmCols, "K slices end in the plane pair");
     static_assert(AE % KE == 0 && PPI == 2, "K slices do not straddle atoms");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
-    static_assert(STAGE_BYTES % 1024 == 0 && OUT_BYTES % 1024 == 0 && B_BYTES % 16 == 0,
+    static_assert(STAGE_BYTES % 1024 == 0 && PART_BYTES % 1024 == 0 && B_BYTES % 16 == 0,
                   "TMA and descriptor alignment");
 };
 static_assert(kUmPlane % 128 == 0 && kUmPlane >= kUmSR * 16, "plane pitch");
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kUmThreads, 1)
     // staging area on a 1024-byte boundary (SMEM includes the slack)
     unsigned char* stages = um_dyn + ((1024u - (um_smem(um_dyn) & 1023u)) & 1023u);
     unsigned char* outstg = stages + C::STAGES * C::STAGE_BYTES;  // output staging, 1024-byte aligned
-    unsigned char* bmat = outstg + C::STG * C::OUT_BYTES;
+    unsigned char* bmat = outstg + C::STG * C::PART_BYTES;
     __shared__ unsigned s_tmem;
     __shared__ volatile int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -470,46 +475,51 @@ __global__ void __launch_bounds__(kUmThreads, 1)
             __syncwarp();
             if (lane == 0) um_bar_arrive(tempty0 + 8u * b);  // accumulator free for the MMAs
             const int x0 = (tile % p.tiles_x) * kUmCols, y0 = (tile / p.tiles_x) * kUmRows;
-            const int sb = C::STG == 2 ? (it & 1) : 0;
-            // the store that last read this staging buffer has finished reading it
-            if (issuer) {
-                if constexpr (C::STG == 2)
-                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-                else
-                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-            }
-            um_epi_sync();
-            const unsigned stg = um_smem(outstg + sb * C::OUT_BYTES);
 #pragma unroll
-            for (int a = 0; a < NAO; ++a) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {  // 16-byte chunk c of this row in atom a
-                    unsigned w[4];
-                    if constexpr (TF32) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const unsigned u = v[a * 32 + c * 4 + i];
-                            w[i] = p.round_out ? um_tf32(__uint_as_float(u)) : u;
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(v[a * 64 + c * 8 + 2 * i]),
-                                                                     __uint_as_float(v[a * 64 + c * 8 + 2 * i + 1]));
-                            w[i] = *reinterpret_cast<unsigned*>(&h);
-                        }
-                    }
-                    um_st_shared_v4(stg + (unsigned)(a * kUmRows * 128 + r * 128 + ((c ^ (r & 7)) << 4)), w[0], w[1],
-                                    w[2], w[3]);
+            for (int part = 0; part < C::PARTS; ++part) {
+                constexpr int APP = NAO / C::PARTS;  // atoms per staged part
+                const int sb = C::STG == 2 ? ((it * C::PARTS + part) & 1) : 0;
+                // the store that last read this staging buffer has finished reading it
+                if (issuer) {
+                    if constexpr (C::STG == 2)
+                        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    else
+                        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                 }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging is read by TMA
-            um_epi_sync();
-            if (issuer) {
+                um_epi_sync();
+                const unsigned stg = um_smem(outstg + sb * C::PART_BYTES);
 #pragma unroll
-                for (int a = 0; a < NAO; ++a)
-                    um_tma_store_2d(&tmap_out, stg + (unsigned)(a * kUmRows * 128), x0 + a * AEO, y0);
-                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                for (int a = 0; a < APP; ++a) {
+                    const int A = part * APP + a;  // atom of the tile
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {  // 16-byte chunk c of this row in atom A
+                        unsigned w[4];
+                        if constexpr (TF32) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const unsigned u = v[A * 32 + c * 4 + i];
+                                w[i] = p.round_out ? um_tf32(__uint_as_float(u)) : u;
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                __nv_bfloat162 h = __floats2bfloat162_rn(
+                                    __uint_as_float(v[A * 64 + c * 8 + 2 * i]), __uint_as_float(v[A * 64 + c * 8 + 2 * i + 1]));
+                                w[i] = *reinterpret_cast<unsigned*>(&h);
+                            }
+                        }
+                        um_st_shared_v4(stg + (unsigned)(a * kUmRows * 128 + r * 128 + ((c ^ (r & 7)) << 4)), w[0],
+                                        w[1], w[2], w[3]);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging is read by TMA
+                um_epi_sync();
+                if (issuer) {
+#pragma unroll
+                    for (int a = 0; a < APP; ++a)
+                        um_tma_store_2d(&tmap_out, stg + (unsigned)(a * kUmRows * 128), x0 + (part * APP + a) * AEO, y0);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
             }
         }
         // every store has completed (and read its staging) before the CTA exits
@@ -532,7 +542,8 @@ __global__ void __launch_bounds__(kUmThreads, 1)
 const void* get_box49_umma_kernel(int tf32, int nt) {
     if (tf32) {
         if (nt == 16) return (const void*)box49_umma_kernel<true, 16>;
-        return nullptr;  // wider TF32 tiles do not fit shared memory with the output staging
+        if (nt == 32) return (const void*)box49_umma_kernel<true, 32>;
+        return nullptr;  // wider TF32 tiles do not fit shared memory
     }
     if (nt == 16) return (const void*)box49_umma_kernel<false, 16>;
     if (nt == 32) return (const void*)box49_umma_kernel<false, 32>;
@@ -541,7 +552,7 @@ const void* get_box49_umma_kernel(int tf32, int nt) {
 }
 
 int box49_umma_smem_bytes(int tf32, int nt) {
-    if (tf32) return UmCfg<true, 16>::SMEM;
+    if (tf32) return nt == 16 ? UmCfg<true, 16>::SMEM : UmCfg<true, 32>::SMEM;
     return nt == 16 ? UmCfg<false, 16>::SMEM : nt == 32 ? UmCfg<false, 32>::SMEM : UmCfg<false, 64>::SMEM;
 }
 

@@ -227,10 +227,11 @@ static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, in
 // Default N of one tcgen05 MMA per operand type (BF16, TF32), and whether
 // that engine is the default for the tensor-core kernel family (kernel = TC or
 // AUTO without autotuning).  Measured on GB300, 16384^2 Box-49, 200 steps:
-// BF16 tcgen05 N = 64 912 GStencil/s (N = 32: 854, N = 16: 615) against 709
-// for the warp-MMA engine; TF32 tcgen05 416 against 420.  Autotuning times both.
-static const int kUmmaDefaultN[2] = {64, 16};
-static const int kUmmaPreferred[2] = {1, 0};
+// BF16 tcgen05 N = 64 916 GStencil/s (N = 32: 856, N = 16: 614) against 708
+// for the warp-MMA engine; TF32 tcgen05 N = 32 492 (N = 16: 417) against 421.
+// Autotuning times both engines.
+static const int kUmmaDefaultN[2] = {64, 32};
+static const int kUmmaPreferred[2] = {1, 1};
 
 // The tcgen05 engine (box49_umma.cu) takes zero-boundary grids whose storage is
 // the MMA operand type (BF16 storage for TC_BF16, FP32 for TC_TF32), with
@@ -253,7 +254,7 @@ static stencil_status_t configure_umma(stencil_plan* p) {
     else if ((p->nx * (int64_t)p->elem) % 16 != 0) why = "the tcgen05 engine needs rows of a multiple of 16 bytes";
     else if (p->ny < 134 || p->nx < 128) why = "the tcgen05 engine needs ny >= 134 and nx >= 128";
     else if (p->opt.mma_n > 0 && !get_box49_umma_kernel(tf32, p->opt.mma_n))
-        why = "no tcgen05 kernel for this mma_n (BF16: 16, 32, 64; TF32: 16)";
+        why = "no tcgen05 kernel for this mma_n (BF16: 16, 32, 64; TF32: 16, 32)";
     if (!why) {
         for (int nt = 16; nt <= 64; nt *= 2) {
             if (p->opt.mma_n > 0 && nt != p->opt.mma_n) continue;

@@ -23,7 +23,7 @@ torch = pytest.importorskip("torch")
 
 TDT = {"f32": "float32", "bf16": "bfloat16"}
 NTS = [("tc_bf16", "bf16", 16), ("tc_bf16", "bf16", 32), ("tc_bf16", "bf16", 64),
-       ("tc_tf32", "f32", 16)]
+       ("tc_tf32", "f32", 16), ("tc_tf32", "f32", 32)]
 
 
 @pytest.fixture(scope="module", autouse=True)
