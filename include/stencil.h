@@ -112,7 +112,10 @@ typedef struct {
     int threads;      /* threads per CTA of the streaming kernel (multiple of 32)   */
     int tile_rows;    /* output rows per CTA tile of the streaming kernel           */
     int autotune;     /* 1: time candidate configurations on first run              */
-    int mma_n;        /* tcgen05 engine: N of one MMA (BF16 16/32/64, TF32 16/32)   */
+    int mma_n;        /* tcgen05 engine: N of the widest MMA.  16, 32, 64 (BF16) or
+                         16, 32 (TF32): one weight row per MMA, 128 x 128 output
+                         tiles; 96 or 128: three or four weight rows stacked in one
+                         MMA over 32-column N-tiles, 126- or 125-row output tiles   */
     int timeout_ms;   /* tcgen05 engine: limit of each device-side wait (0 = 2000)  */
     int debug_withhold; /* test hook, 0 in normal use: 1 makes CTA 0 of the tcgen05
                            engine withhold its first accumulator-ready signal, so its

@@ -263,19 +263,21 @@ __device__ __forceinline__ void um_ld32(unsigned taddr, unsigned* r) {
 
 __device__ __forceinline__ void um_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Named barrier 1 over the 128 epilogue threads; returns the AND of `pred`.
+// Named barrier 1 over the NTH epilogue threads; returns the AND of `pred`.
+template <int NTH = 128>
 __device__ __forceinline__ int um_epi_and(int pred) {
     int r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 128, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        "bar.red.and.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"(pred)
+        : "r"(pred), "n"(NTH)
         : "memory");
     return r;
 }
 
-__device__ __forceinline__ void um_epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+template <int NTH = 128>
+__device__ __forceinline__ void um_epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NTH) : "memory"); }
 
 __device__ __forceinline__ void um_tma_store_2d(const CUtensorMap* map, unsigned src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
@@ -536,6 +538,365 @@ __global__ void __launch_bounds__(kUmThreads, 1)
     }
 }
 
+// ---- row-grouped variant ------------------------------------------------------------------
+//
+// The kernel above reads its A operand (128 rows x one K slice, 4 KB) from
+// shared memory once per (N-tile, K step, weight row), and that read, not
+// the arithmetic, sets the cost of an MMA.  Here D weight rows share one
+// read: the B operand stacks the Toeplitz bands of rows s .. s+D-1 side by
+// side (N = D * NT columns) and A is the staged tile shifted by s rows.
+// Column block d of the accumulator then holds, in TMEM lane r, what staged
+// row r + s contributes through weight row s + d, which belongs to output
+// row r - d.  So
+//   out[r] = sum_d acc_d[r + d],   r = 0 .. 128 - D,
+// a tile has 129 - D output rows, and the epilogue adds the D blocks with
+// lane shifts: warp shuffles inside a lane quarter; the last d lanes of a
+// quarter take the first d lanes of the next one through shared memory.
+// The rows form groups {0..D-1}, {D..2D-1}, ..; the last group may hold
+// fewer rows (a narrower MMA that adds into the leading blocks).  Each
+// accumulator holds one N-tile (D * NT columns), up to four in flight.
+// Measured on GB300 (16384^2, 200 steps): TF32 N = 96 (D = 3) 547 GStencil/s
+// against 492 for one row per MMA; BF16 N = 96 784 and N = 128 596 against
+// 916.  With the epilogue's shuffles and exchange taken out (a timing copy)
+// BF16 reaches only ~940 (D = 3) and ~1130 (D = 4): the wider MMAs cost more
+// than the A reads they save, and the D - 1 shuffles per output halve the
+// rest.  Eight epilogue warps instead of four, and adding the in-quarter
+// terms before the exchange barrier, were both slower.
+template <bool TF32, int NT, int D>
+struct UmgCfg {
+    static constexpr int EB = TF32 ? 4 : 2;
+    static constexpr int EPG = 16 / EB;
+    static constexpr int L = TF32 ? 4 : 8;
+    static constexpr int KE = TF32 ? 8 : 16;
+    static constexpr int KSTEPS = (NT + L + 3 + KE - 1) / KE;
+    static constexpr int PPI = KE / EPG;
+    static constexpr int JT = kUmCols / NT;
+    static constexpr int AE = 128 / EB;
+    static constexpr int NA = kUmCols / AE;
+    static constexpr int NG = (7 + D - 1) / D;                   // row groups
+    static constexpr int OUT = kUmRows + 1 - D;                   // output rows per tile
+    static constexpr int BUFN = D * NT;                           // TMEM columns of one N-tile
+    static constexpr int NBUF = 512 / BUFN < 4 ? 512 / BUFN : 4;  // accumulators in flight
+    static constexpr int STAGES = TF32 ? 2 : 3;
+    static constexpr int STAGE_BYTES = (NA * kUmAtom + PPI * kUmPlane + 1023) / 1024 * 1024;
+    static constexpr int TX_BYTES = NA * kUmSR * 128 + PPI * kUmSR * 16;
+    static constexpr int ROW_BYTES = KSTEPS * PPI * NT * 16;      // B bytes per weight row
+    static constexpr int B_BYTES = 7 * ROW_BYTES;
+    static constexpr int XQ = (D - 1) * (D - 1) * 32;             // exchange floats per lane quarter
+    static constexpr int XCH_BYTES = 2 * 4 * XQ * 4;              // two parities x four quarters
+    static constexpr int NBARS = 2 * STAGES + 2 * NBUF + 1;
+    static constexpr int OUT_BYTES = kUmRows * kUmCols * EB;
+    static constexpr int BASE = STAGES * STAGE_BYTES + B_BYTES + XCH_BYTES + 8 * NBARS;
+    static constexpr int LIMIT = 227 * 1024 - 1024;               // dynamic bytes next to the static ones
+    static constexpr int PARTS = 1024 + BASE + OUT_BYTES <= LIMIT ? 1 : 2;
+    static constexpr int PART_BYTES = OUT_BYTES / PARTS;
+    static constexpr int STG = 1024 + BASE + 2 * PART_BYTES <= LIMIT ? 2 : 1;
+    static constexpr int SMEM = 1024 + BASE + STG * PART_BYTES;
+    static __host__ __device__ constexpr int rows(int g) { return 7 - g * D < D ? 7 - g * D : D; }
+    static_assert(D >= 2 && D <= 7 && NT % 32 == 0 && BUFN <= 256 && NBUF >= 2, "group shape");
+    static_assert((JT - 1) * NT + (KSTEPS - 1) * KE <= kUmCols, "K slices end in the plane pair");
+    static_assert(AE % KE == 0 && PPI == 2, "K slices do not straddle atoms");
+    static_assert(kUmCols % (kUmCols / PARTS) == 0 && (kUmCols / PARTS) % NT == 0, "parts hold whole N-tiles");
+    static_assert(SMEM <= LIMIT, "shared memory per CTA");
+    static_assert(STAGE_BYTES % 1024 == 0 && PART_BYTES % 1024 == 0 && ROW_BYTES % 16 == 0 &&
+                      (STAGES * STAGE_BYTES + STG * PART_BYTES + B_BYTES) % 16 == 0,
+                  "TMA and descriptor alignment");
+};
+
+template <bool TF32>
+__device__ __forceinline__ unsigned um_idesc_n(int n) {
+    constexpr unsigned ab = TF32 ? 2u : 1u;
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(kUmRows >> 4) << 24);
+}
+
+template <bool TF32, int NT, int D>
+__global__ void __launch_bounds__(kUmThreads, 1)
+    box49_umma_rows_kernel(const __grid_constant__ CUtensorMap tmap_sw, const __grid_constant__ CUtensorMap tmap_pl,
+                           const __grid_constant__ CUtensorMap tmap_out, const __grid_constant__ UmParams p) {
+    using C = UmgCfg<TF32, NT, D>;
+    extern __shared__ __align__(1024) unsigned char um_dyn[];
+    unsigned char* stages = um_dyn + ((1024u - (um_smem(um_dyn) & 1023u)) & 1023u);
+    unsigned char* outstg = stages + C::STAGES * C::STAGE_BYTES;
+    unsigned char* bmat = outstg + C::STG * C::PART_BYTES;
+    float* xch = reinterpret_cast<float*>(bmat + C::B_BYTES);
+    __shared__ unsigned s_tmem;
+    __shared__ volatile int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // barriers: full[S], empty[S], tmem_full[NBUF], tmem_empty[NBUF], drain
+    const unsigned bar0 = um_smem(bmat + C::B_BYTES + C::XCH_BYTES);
+    const unsigned full0 = bar0, empty0 = bar0 + 8u * C::STAGES, tfull0 = bar0 + 16u * C::STAGES,
+                   tempty0 = tfull0 + 8u * C::NBUF, drain = tempty0 + 8u * C::NBUF;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < C::STAGES; ++s) {
+            um_bar_init(full0 + 8u * s, 1);
+            um_bar_init(empty0 + 8u * s, 1);
+        }
+        for (int b = 0; b < C::NBUF; ++b) {
+            um_bar_init(tfull0 + 8u * b, 1);
+            um_bar_init(tempty0 + 8u * b, 4);
+        }
+        um_bar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // B of row group g (rows g*D .. g*D + rows(g) - 1) starts at byte
+    // g * D * ROW_BYTES; K-major, no swizzle, plane pitch rows(g) * NT * 16:
+    // element (k, n) at (k / EPG) * pitch + 16 n + EB * (k % EPG), where
+    // n = d * NT + n' holds W[g*D + d][k - n' - (L - 3)] (0 outside the band).
+    for (int i = threadIdx.x; i < 7 * C::KSTEPS * C::PPI * NT * C::EPG; i += kUmThreads) {
+        const int e = i % C::EPG;
+        const int n1 = (i / C::EPG) % NT;
+        const int pl = (i / (C::EPG * NT)) % (C::KSTEPS * C::PPI);
+        const int di = i / (C::EPG * NT * C::KSTEPS * C::PPI);
+        const int g = di / D, d = di % D;
+        const int dj = pl * C::EPG + e - n1 - (C::L - 3);
+        const float v = (dj >= 0 && dj <= 6) ? p.w[di * 7 + dj] : 0.f;
+        unsigned char* dst = bmat + g * D * C::ROW_BYTES + pl * (C::rows(g) * NT * 16) + (d * NT + n1) * 16 + e * C::EB;
+        if constexpr (TF32) {
+            *reinterpret_cast<unsigned*>(dst) = um_tf32(v);
+        } else {
+            *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(um_smem(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    um_fence_before();
+    __syncthreads();
+    um_fence_after();
+    const unsigned tmem = s_tmem;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        int it = 0;
+        for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, ++it) {
+            const int s = it % C::STAGES;
+            int ok = 1;
+            if (lane == 0) ok = um_wait(empty0 + 8u * s, ((it / C::STAGES) & 1) ^ 1, &s_abort, p.status, p.wait_ns);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            if (lane == 0) {
+                const int x0 = (tile % p.tiles_x) * kUmCols, y0 = (tile / p.tiles_x) * C::OUT;
+                const unsigned fb = full0 + 8u * s;
+                const unsigned dst = um_smem(stages + s * C::STAGE_BYTES);
+                if ((dst & 1023u) != 0u || (fb & 7u) != 0u) {
+                    atomicCAS(p.status, 0u, (unsigned)STENCIL_ERR_DEVICE_CHECK);
+                    s_abort = 1;
+                    ok = 0;
+                } else {
+                    um_bar_expect_tx(fb, (unsigned)C::TX_BYTES);
+                    const int xs = x0 - C::L;
+                    for (int a = 0; a < C::NA; ++a)
+                        um_tma_2d(dst + (unsigned)(a * kUmAtom), &tmap_sw, xs + C::AE * a, y0 - 3, fb);
+                    for (int g = 0; g < C::PPI; ++g)
+                        um_tma_2d(dst + (unsigned)(C::NA * kUmAtom + g * kUmPlane), &tmap_pl,
+                                  xs + kUmCols + C::EPG * g, y0 - 3, fb);
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        }
+        if (lane == 0) {
+            for (int i = it - C::STAGES < 0 ? 0 : it - C::STAGES; i < it; ++i)
+                um_drain(full0 + 8u * (i % C::STAGES), (i / C::STAGES) & 1, p.status, p.wait_ns);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issue (one thread) ----------------
+        int it = 0, u = 0, issued = 0;
+        bool alive = true;
+        for (int tile = blockIdx.x; tile < p.tiles && alive; tile += gridDim.x, ++it) {
+            const int s = it % C::STAGES;
+            int ok = 1;
+            if (lane == 0) ok = um_wait(full0 + 8u * s, (it / C::STAGES) & 1, &s_abort, p.status, p.wait_ns);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            const unsigned sbase = um_smem(stages + s * C::STAGE_BYTES);
+            for (int j = 0; j < C::JT; ++j, ++u) {
+                const int bf = u % C::NBUF;
+                if (lane == 0) ok = um_wait(tempty0 + 8u * bf, ((u / C::NBUF) & 1) ^ 1, &s_abort, p.status, p.wait_ns);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    alive = false;
+                    break;
+                }
+                um_fence_after();
+                if (lane == 0) {
+                    const unsigned dcol = tmem + (unsigned)(bf * C::BUFN);
+#pragma unroll
+                    for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                        const int c = NT * j + C::KE * ks;  // first column of the K slice (from x0 - L)
+#pragma unroll
+                        for (int g = 0; g < C::NG; ++g) {
+                            const int sh = g * D;  // row shift of A for this group
+                            const unsigned long long a =
+                                c < kUmCols ? um_desc_sw128(sbase + (unsigned)((c / C::AE) * kUmAtom + 128 * sh +
+                                                                               (c % C::AE) * C::EB))
+                                            : um_desc(sbase + (unsigned)(C::NA * kUmAtom + 16 * sh), kUmPlane, 128);
+                            const unsigned pitch = (unsigned)(C::rows(g) * NT * 16);
+                            const unsigned long long bd =
+                                um_desc(um_smem(bmat) + (unsigned)(sh * C::ROW_BYTES) + (unsigned)(ks * C::PPI) * pitch,
+                                        pitch, 128);
+                            um_mma<TF32>(dcol, a, bd, um_idesc_n<TF32>(C::rows(g) * NT), (ks | g) != 0);
+                        }
+                    }
+                    if (!(p.withhold && blockIdx.x == 0 && u == 0)) um_commit(tfull0 + 8u * bf);
+                    issued = 1;
+                }
+                __syncwarp();
+            }
+            if (!alive) break;
+            if (lane == 0) um_commit(empty0 + 8u * s);  // the stage is free once these MMAs have read it
+            __syncwarp();
+        }
+        if (lane == 0 && issued) {
+            um_commit(drain);
+            um_drain(drain, 0, p.status, p.wait_ns);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: TMEM lanes 32 q .. 32 q + 31 ----------------
+        // Per N-tile: load the D column blocks of the thread's lane (one wait),
+        // free the accumulator, pass lanes 0 .. D-2 to the quarter above, add
+        // the blocks with lane shifts and write the row into the swizzled
+        // staging tile; one thread stores each finished part with TMA.
+        const int q = warp & 3;
+        const int r = 32 * q + lane;                 // TMEM lane = output row of block 0
+        const bool issuer = threadIdx.x == 64;
+        constexpr int AEO = 128 / C::EB;             // output columns per staged atom
+        constexpr int EPC = 16 / C::EB;              // output columns per 16-byte chunk
+        constexpr int CPC = 32 / EPC;                // chunks per 32 columns
+        constexpr int PW = kUmCols / C::PARTS;       // columns per staged part
+        constexpr int APP = PW / AEO;                // atoms per staged part
+        int it = 0, u = 0, xpar = 0;
+        bool alive = true;
+        for (int tile = blockIdx.x; tile < p.tiles && alive; tile += gridDim.x, ++it) {
+            const int x0 = (tile % p.tiles_x) * kUmCols, y0 = (tile / p.tiles_x) * C::OUT;
+            for (int j = 0; j < C::JT; ++j, ++u) {
+                const int part = (NT * j) / PW;
+                const int sb = C::STG == 2 ? ((it * C::PARTS + part) & 1) : 0;
+                const unsigned stg = um_smem(outstg + sb * C::PART_BYTES);
+                if ((NT * j) % PW == 0) {
+                    // the store that last read this staging buffer has finished reading it
+                    if (issuer) {
+                        if constexpr (C::STG == 2)
+                            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        else
+                            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    }
+                    um_epi_sync();
+                }
+                const int bf = u % C::NBUF;
+                int ok = 1;
+                if (lane == 0) ok = um_wait(tfull0 + 8u * bf, (u / C::NBUF) & 1, &s_abort, p.status, p.wait_ns);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!um_epi_and(ok)) {  // the four epilogue warps leave together
+                    alive = false;
+                    break;
+                }
+                um_fence_after();
+#pragma unroll 1
+                for (int ch = 0; ch < NT / 32; ++ch) {
+                    unsigned v[D][32];
+                    const unsigned tb = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(bf * C::BUFN + 32 * ch);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) um_ld32(tb + (unsigned)(d * NT), v[d]);
+                    um_ld_wait();
+                    if (ch == NT / 32 - 1) {
+                        um_fence_before();
+                        __syncwarp();
+                        if (lane == 0) um_bar_arrive(tempty0 + 8u * bf);  // accumulator free for the MMAs
+                    }
+                    // lanes l < d of block d feed rows 32 q + l + 32 - d of the quarter below
+                    float* xw = xch + (xpar * 4 + q) * C::XQ;
+#pragma unroll
+                    for (int d = 1; d < D; ++d) {
+                        if (lane < d) {
+                            float4* dst = reinterpret_cast<float4*>(xw + ((d - 1) * (D - 1) + lane) * 32);
+#pragma unroll
+                            for (int n = 0; n < 8; ++n)
+                                dst[n] = make_float4(__uint_as_float(v[d][4 * n]), __uint_as_float(v[d][4 * n + 1]),
+                                                     __uint_as_float(v[d][4 * n + 2]), __uint_as_float(v[d][4 * n + 3]));
+                        }
+                    }
+                    um_epi_sync();
+                    // quarter 3 reads quarter 0 here only for rows >= OUT, which are never stored
+                    const float* xr = xch + (xpar * 4 + ((q + 1) & 3)) * C::XQ;
+                    xpar ^= 1;
+                    float o[32];
+#pragma unroll
+                    for (int n = 0; n < 32; ++n) o[n] = __uint_as_float(v[0][n]);
+#pragma unroll
+                    for (int d = 1; d < D; ++d) {
+                        const bool top = lane + d >= 32;  // row r + d lies in the next quarter
+                        const float4* src =
+                            reinterpret_cast<const float4*>(xr + ((d - 1) * (D - 1) + (top ? lane + d - 32 : 0)) * 32);
+#pragma unroll
+                        for (int n = 0; n < 8; ++n) {
+                            float s0 = __shfl_down_sync(0xffffffffu, __uint_as_float(v[d][4 * n]), d);
+                            float s1 = __shfl_down_sync(0xffffffffu, __uint_as_float(v[d][4 * n + 1]), d);
+                            float s2 = __shfl_down_sync(0xffffffffu, __uint_as_float(v[d][4 * n + 2]), d);
+                            float s3 = __shfl_down_sync(0xffffffffu, __uint_as_float(v[d][4 * n + 3]), d);
+                            if (top) {
+                                const float4 t = src[n];
+                                s0 = t.x;
+                                s1 = t.y;
+                                s2 = t.z;
+                                s3 = t.w;
+                            }
+                            o[4 * n] += s0;
+                            o[4 * n + 1] += s1;
+                            o[4 * n + 2] += s2;
+                            o[4 * n + 3] += s3;
+                        }
+                    }
+                    const int col0 = NT * j + 32 * ch;  // tile column of o[0]
+                    const int a = (col0 / AEO) % APP;   // atom in the staged part
+                    const int c0 = (col0 % AEO) / EPC;  // its first 16-byte chunk in the row
+#pragma unroll
+                    for (int c = 0; c < CPC; ++c) {
+                        unsigned w[4];
+                        if constexpr (TF32) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                w[i] = p.round_out ? um_tf32(o[4 * c + i]) : __float_as_uint(o[4 * c + i]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                __nv_bfloat162 h = __floats2bfloat162_rn(o[8 * c + 2 * i], o[8 * c + 2 * i + 1]);
+                                w[i] = *reinterpret_cast<unsigned*>(&h);
+                            }
+                        }
+                        um_st_shared_v4(stg + (unsigned)(a * kUmRows * 128 + r * 128 + (((c0 + c) ^ (r & 7)) << 4)),
+                                        w[0], w[1], w[2], w[3]);
+                    }
+                }
+                if ((NT * (j + 1)) % PW == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staging is read by TMA
+                    um_epi_sync();
+                    if (issuer) {
+#pragma unroll
+                        for (int a = 0; a < APP; ++a)
+                            um_tma_store_2d(&tmap_out, stg + (unsigned)(a * kUmRows * 128), x0 + (part * APP + a) * AEO,
+                                            y0);
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                }
+            }
+        }
+        if (issuer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
+    }
+
+    um_fence_before();
+    __syncthreads();
+    um_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
 // ---- host side ----------------------------------------------------------------------------
 
 // Kernel for (tf32, nt), or NULL when that pair is not instantiated.
@@ -543,20 +904,34 @@ const void* get_box49_umma_kernel(int tf32, int nt) {
     if (tf32) {
         if (nt == 16) return (const void*)box49_umma_kernel<true, 16>;
         if (nt == 32) return (const void*)box49_umma_kernel<true, 32>;
-        return nullptr;  // wider TF32 tiles do not fit shared memory
+        if (nt == 96) return (const void*)box49_umma_rows_kernel<true, 32, 3>;
+        if (nt == 128) return (const void*)box49_umma_rows_kernel<true, 32, 4>;
+        return nullptr;  // wider one-row TF32 tiles do not fit shared memory
     }
     if (nt == 16) return (const void*)box49_umma_kernel<false, 16>;
     if (nt == 32) return (const void*)box49_umma_kernel<false, 32>;
     if (nt == 64) return (const void*)box49_umma_kernel<false, 64>;
+    if (nt == 96) return (const void*)box49_umma_rows_kernel<false, 32, 3>;
+    if (nt == 128) return (const void*)box49_umma_rows_kernel<false, 32, 4>;
     return nullptr;
 }
 
 int box49_umma_smem_bytes(int tf32, int nt) {
-    if (tf32) return nt == 16 ? UmCfg<true, 16>::SMEM : UmCfg<true, 32>::SMEM;
+    if (tf32) {
+        if (nt == 96) return UmgCfg<true, 32, 3>::SMEM;
+        if (nt == 128) return UmgCfg<true, 32, 4>::SMEM;
+        return nt == 16 ? UmCfg<true, 16>::SMEM : UmCfg<true, 32>::SMEM;
+    }
+    if (nt == 96) return UmgCfg<false, 32, 3>::SMEM;
+    if (nt == 128) return UmgCfg<false, 32, 4>::SMEM;
     return nt == 16 ? UmCfg<false, 16>::SMEM : nt == 32 ? UmCfg<false, 32>::SMEM : UmCfg<false, 64>::SMEM;
 }
 
-int box49_umma_threads() { return kUmThreads; }
+// Output rows per tile: 128 for one weight row per MMA (N <= 64), 129 - D for
+// D = N / 32 rows per MMA.
+int box49_umma_tile_rows(int nt) { return nt > 64 ? kUmRows + 1 - nt / 32 : kUmRows; }
+
+int box49_umma_threads(int) { return kUmThreads; }
 
 static PFN_cuTensorMapEncodeTiled_v12000 um_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -601,8 +976,8 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
     alignas(64) CUtensorMap map_sw, map_pl, map_out;
     if (um_encode(enc, &map_sw, tf32, src, ny, nx, ld, 128 / eb, kUmSR, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
         um_encode(enc, &map_pl, tf32, src, ny, nx, ld, 16 / eb, kUmSR, CU_TENSOR_MAP_SWIZZLE_NONE) != CUDA_SUCCESS ||
-        um_encode(enc, &map_out, tf32, dst, ny, nx, ld, 128 / eb, kUmRows, CU_TENSOR_MAP_SWIZZLE_128B) !=
-            CUDA_SUCCESS)
+        um_encode(enc, &map_out, tf32, dst, ny, nx, ld, 128 / eb, box49_umma_tile_rows(nt),
+                  CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
     UmParams up{};
     up.out = dst;
@@ -610,7 +985,7 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
     up.nx = nx;
     up.ld = ld;
     up.tiles_x = (nx + kUmCols - 1) / kUmCols;
-    up.tiles = up.tiles_x * ((ny + kUmRows - 1) / kUmRows);
+    up.tiles = up.tiles_x * ((ny + box49_umma_tile_rows(nt) - 1) / box49_umma_tile_rows(nt));
     up.round_out = round_out;
     up.status = status;
     up.wait_ns = (long long)(timeout_ms > 0 ? timeout_ms : 2000) * 1000000LL;
@@ -618,7 +993,7 @@ cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int 
     for (int i = 0; i < 49; ++i) up.w[i] = w[i];
     void* args[] = {&map_sw, &map_pl, &map_out, &up};
     const int grid = ctas < up.tiles ? ctas : up.tiles;
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kUmThreads), args,
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)box49_umma_threads(nt)), args,
                             (size_t)box49_umma_smem_bytes(tf32, nt), st);
 }
 

@@ -36,7 +36,8 @@ const void* get_box49_tc_pipe_kernel(int dtype, int engine);
 int box49_tc_smem_bytes(int engine);
 const void* get_box49_umma_kernel(int tf32, int nt);
 int box49_umma_smem_bytes(int tf32, int nt);
-int box49_umma_threads();
+int box49_umma_threads(int nt);
+int box49_umma_tile_rows(int nt);
 cudaError_t launch_box49_umma(int tf32, int nt, const void* src, void* dst, int ny, int nx, int ld,
                               int round_out, unsigned* status, const float* w, int ctas, cudaStream_t st,
                               int timeout_ms, int withhold);
@@ -227,10 +228,14 @@ static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, in
 // Default N of one tcgen05 MMA per operand type (BF16, TF32), and whether
 // that engine is the default for the tensor-core kernel family (kernel = TC or
 // AUTO without autotuning).  Measured on GB300, 16384^2 Box-49, 200 steps:
-// BF16 tcgen05 N = 64 916 GStencil/s (N = 32: 856, N = 16: 614) against 708
-// for the warp-MMA engine; TF32 tcgen05 N = 32 492 (N = 16: 417) against 421.
-// Autotuning times both engines.
-static const int kUmmaDefaultN[2] = {64, 32};
+// BF16 tcgen05 N = 64 916 GStencil/s (N = 32: 856, N = 16: 614; three or four
+// weight rows per MMA, N = 96: 784, N = 128: 596) against 708 for the warp-MMA
+// engine; TF32 tcgen05 N = 96 547 (N = 32: 492, N = 16: 417, N = 128: 457)
+// against 421.  Autotuning times both engines and every width.
+static const int kUmmaDefaultN[2] = {64, 96};
+// MMA widths of the tcgen05 kernels: N = 16, 32, 64 with one weight row per
+// MMA; N = 96 and 128 stack three or four weight rows over 32-column N-tiles.
+static const int kUmmaWidths[5] = {16, 32, 64, 96, 128};
 static const int kUmmaPreferred[2] = {1, 1};
 
 // The tcgen05 engine (box49_umma.cu) takes zero-boundary grids whose storage is
@@ -254,16 +259,16 @@ static stencil_status_t configure_umma(stencil_plan* p) {
     else if ((p->nx * (int64_t)p->elem) % 16 != 0) why = "the tcgen05 engine needs rows of a multiple of 16 bytes";
     else if (p->ny < 134 || p->nx < 128) why = "the tcgen05 engine needs ny >= 134 and nx >= 128";
     else if (p->opt.mma_n > 0 && !get_box49_umma_kernel(tf32, p->opt.mma_n))
-        why = "no tcgen05 kernel for this mma_n (BF16: 16, 32, 64; TF32: 16, 32)";
+        why = "no tcgen05 kernel for this mma_n (BF16: 16, 32, 64, 96, 128; TF32: 16, 32, 96, 128)";
     if (!why) {
-        for (int nt = 16; nt <= 64; nt *= 2) {
+        for (int nt : kUmmaWidths) {
             if (p->opt.mma_n > 0 && nt != p->opt.mma_n) continue;
             const void* fn = get_box49_umma_kernel(tf32, nt);
             if (!fn) continue;
             const int smem = box49_umma_smem_bytes(tf32, nt);
             CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             int per_sm = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, box49_umma_threads(), smem));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, box49_umma_threads(nt), smem));
             if (per_sm >= 1) p->umma_ok |= 1 << (nt / 16);
         }
         if (!p->umma_ok) why = "the tcgen05 kernel does not fit an SM";
@@ -272,7 +277,8 @@ static stencil_status_t configure_umma(stencil_plan* p) {
         if (want == STENCIL_KERNEL_TC_UMMA) return fail(STENCIL_ERR_UNSUPPORTED, why);
         return STENCIL_OK;
     }
-    // One CTA per SM: each holds 256 tensor-memory columns for its whole life.
+    // One CTA per SM: each holds 256 (one weight row per MMA) or 512 (row
+    // groups) tensor-memory columns for its whole life.
     p->umma_ctas = (int)std::min<int64_t>((int64_t)p->sms, (int64_t)p->strips * p->tiles_y);
     const int nt = p->opt.mma_n > 0 ? p->opt.mma_n : kUmmaDefaultN[tf32];
     if (want == STENCIL_KERNEL_TC_UMMA || kUmmaPreferred[tf32]) p->umma_n = (p->umma_ok >> (nt / 16)) & 1 ? nt : 0;
@@ -542,7 +548,8 @@ static stencil_status_t autotune_tc(stencil_plan* p, const void* in, cudaStream_
     if (best_n < 0) {
         const int reps = (int)std::max(2.0, std::min(32.0, 4e9 / ((double)p->ny * (double)p->nx)));
         float best = 1e30f;
-        for (int nt = 0; nt <= 64; nt = nt ? 2 * nt : 16) {
+        for (int c = 0; c <= 5; ++c) {
+            const int nt = c ? kUmmaWidths[c - 1] : 0;
             if (nt && !((p->umma_ok >> (nt / 16)) & 1)) continue;
             p->umma_n = nt;
             cudaEvent_t e0, e1;
@@ -846,9 +853,10 @@ stencil_status_t stencil_plan_info(const stencil_plan_t* p, stencil_plan_info_t*
         i.smem_bytes = p->res_smem;
     }
     if (p->umma_n) {
-        i.threads = box49_umma_threads();
+        i.threads = box49_umma_threads(p->umma_n);
         i.ctas = p->umma_ctas;
         i.smem_bytes = box49_umma_smem_bytes(p->compute == STENCIL_COMPUTE_TC_TF32, p->umma_n);
+        i.tile_rows = box49_umma_tile_rows(p->umma_n);
     }
     *info = i;
     return STENCIL_OK;

@@ -22,8 +22,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TDT = {"f32": "float32", "bf16": "bfloat16"}
+# N = 16, 32, 64: one weight row per MMA; 96, 128: three or four rows per MMA
 NTS = [("tc_bf16", "bf16", 16), ("tc_bf16", "bf16", 32), ("tc_bf16", "bf16", 64),
-       ("tc_tf32", "f32", 16), ("tc_tf32", "f32", 32)]
+       ("tc_bf16", "bf16", 96), ("tc_bf16", "bf16", 128),
+       ("tc_tf32", "f32", 16), ("tc_tf32", "f32", 32), ("tc_tf32", "f32", 96), ("tc_tf32", "f32", 128)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +66,7 @@ def test_engine_selection():
     W = inputs.pattern_weights("box49")
     p = _plan((300, 392), W, "tc_bf16", "bf16", kernel="tc_umma")
     i = p.info()
-    assert i["kernel"] == 5 and i["mma_n"] in (16, 32, 64) and i["threads"] == 192
+    assert i["kernel"] == 5 and i["mma_n"] in (16, 32, 64, 96, 128) and i["threads"] == 192
     assert 1 <= i["ctas"] <= torch.cuda.get_device_properties(0).multi_processor_count
     p.close()
     p = _plan((300, 392), W, "tc_bf16", "bf16")  # default: the faster engine as measured
@@ -92,6 +94,10 @@ def test_engine_selection():
     p = _plan((300, 392), W, "tc_tf32", "f32", kernel="tc", mma_n=64)  # not instantiated: warp MMAs
     assert p.info()["kernel"] == 3
     p.close()
+    for nt, rows in ((64, 128), (96, 126), (128, 125)):
+        p = _plan((300, 392), W, "tc_bf16", "bf16", kernel="tc_umma", mma_n=nt)
+        assert p.info()["tile_rows"] == rows
+        p.close()
 
 
 @pytest.mark.parametrize("compute,dtype,nt", NTS)
