@@ -305,7 +305,8 @@ def run_variant(args, world, rank, local):
             kern = {"auto": "auto", "warp": "tc_warp", "umma": "tc_umma"}[args.tc_engine] \
                 if compute.startswith("tc") else "auto"
             plans[pn] = Plan(n, n, inputs.pattern_weights(pn), dtype=dtype, compute=compute, kernel=kern,
-                             autotune=not args.no_autotune)
+                             autotune=not args.no_autotune,
+                             mma_n=args.mma_n if compute.startswith("tc") else 0)
             hins[pn] = torch.from_numpy(f).to(tdt).pin_memory()
             xs[pn] = hins[pn].cuda()
             outs[pn] = torch.empty_like(xs[pn])
@@ -353,7 +354,8 @@ def run_variant(args, world, rank, local):
                                        "note": f"{2 * esz} B per point-step x {k} steps per launch "
                                                f"({pats[0]})",
                                        "traffic": _ncu_traffic(
-                                           f"box49_{'umma' if info0['kernel'] == 5 else 'warp'}_{dtype}_{n}")
+                                           f"box49_umma_n{info0['mma_n']}_{dtype}_{n}" if info0["kernel"] == 5
+                                           else f"box49_warp_{compute}_{n}")
                                        if compute.startswith("tc") else None},
             "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
                     "h2d_bytes_per_step": len(pats) * n * n * esz, "d2h_bytes_per_step": len(pats) * n * n * esz,
@@ -492,6 +494,8 @@ def main():
                     help="headline workload: fixed temporal-blocking depth (profiling captures)")
     ap.add_argument("--tc-engine", default="auto", choices=["auto", "warp", "umma"],
                     help="tensor-core workloads: autotuned engine choice, warp-level MMAs, or tcgen05")
+    ap.add_argument("--mma-n", type=int, default=0,
+                    help="tensor-core workloads: fixed tcgen05 MMA width (16, 32, 64, 96, 128; 0 = choose)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
