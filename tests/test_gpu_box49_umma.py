@@ -178,24 +178,26 @@ def test_autotune_picks_an_engine_and_stays_exact(oracle, compute, dtype):
     p.close()
 
 
-def test_expired_wait_reports_timeout_and_device_recovers(oracle):
+@pytest.mark.parametrize("nt", [64, 96])
+def test_expired_wait_reports_timeout_and_device_recovers(oracle, nt):
     """Failure detection without a fault: with the test hook, CTA 0 never
     signals its first accumulator, so its epilogue wait runs out after
     timeout_ms; the kernel drains its own copies and MMAs, frees its tensor
     memory and returns, the plan reports TIMEOUT, and the device then runs a
-    normal plan with exact results."""
+    normal plan with exact results.  N = 64: one weight row per MMA; N = 96:
+    row groups, whose MMA warp is then blocked on a later accumulator."""
     from paper_2605_07954_gb300 import Plan, StencilError
     shape = (300, 392)
     u0, W = _dyadic(shape, 17)
     x = _to_dev(u0, "bf16")
     bad = Plan(shape[0], shape[1], W, dtype="bf16", compute="tc_bf16", kernel="tc_umma",
-               timeout_ms=100, debug_withhold=1)
+               timeout_ms=100, debug_withhold=1, mma_n=nt)
     bad.run(x, 1)
     torch.cuda.synchronize()
     with pytest.raises(StencilError, match="TIMEOUT"):
         bad.status()
     bad.close()
-    good = _plan(shape, W, "tc_bf16", "bf16", kernel="tc_umma")
+    good = _plan(shape, W, "tc_bf16", "bf16", kernel="tc_umma", mma_n=nt)
     got = good.run(x, 2).float().cpu().numpy().astype(np.float64)
     torch.cuda.synchronize()
     good.status()
