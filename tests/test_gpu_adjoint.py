@@ -55,6 +55,26 @@ def test_gradients_match_oracle(oracle, name, boundary):
     assert rel_l2(gw, ref_w) <= 1e-4
 
 
+@pytest.mark.parametrize("boundary", ["zero", "periodic"])
+@pytest.mark.parametrize("shape", [(70, 132), (5, 8), (129, 260), (64, 4)])
+@pytest.mark.parametrize("name", ["heat5", "box9"])
+def test_row_streamed_step_ragged_shapes(oracle, name, shape, boundary):
+    """Radius 1 with widths that are a multiple of 4 takes the row-streaming
+    reverse step: 128-column strips and 64-row tiles that the shapes cut
+    unevenly, strips wider than the grid, grids shorter than a warp's rows;
+    both gradients against the FP64 oracle."""
+    W = inputs.pattern_weights(name)
+    u0 = inputs.field(*shape)
+    target = inputs.field(*shape, stream=inputs.STREAM_TARGET)
+    T = 12
+    uT = oracle.sweep_f64(u0, W, T, boundary)
+    gT = (uT - target).astype(np.float32)
+    ref_u, ref_w = oracle.adjoint_f64(u0, W, T, gT.astype(np.float64), boundary)
+    gu, gw = _grads(u0, W, T, gT, boundary)
+    assert rel_l2(gu, ref_u) <= 1e-5
+    assert rel_l2(gw, ref_w) <= 1e-5
+
+
 def test_checkpoint_interval_does_not_change_bits():
     W = inputs.pattern_weights("box9")
     u0 = inputs.field(100, 130)
