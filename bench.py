@@ -154,6 +154,14 @@ def whole_job_rate(world: int, units_per_rank: float, max_ms: float) -> float:
     return world * units_per_rank / (max_ms * 1e-3) / 1e9
 
 
+def window_error(got, ref) -> dict:
+    """Relative L2 and L-infinity error of a window against its FP64 reference."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return {"relL2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "relLinf": float(np.abs(got - ref).max() / np.abs(ref).max())}
+
+
 def cpu_oracle_sample(steps_per_pattern: int = 40, n: int = N):
     """The FP32 oracle, as it stands, on n x n grids for a few steps of each pattern."""
     import oracle
@@ -492,6 +500,11 @@ def main():
                     help="box9+star13 (the headline) or one of the variant workloads")
     ap.add_argument("--tb-depth", type=int, default=0,
                     help="headline workload: fixed temporal-blocking depth (profiling captures)")
+    ap.add_argument("--threads", type=int, default=0,
+                    help="headline workload: fixed CTA size of the streaming kernel (profiling captures)")
+    ap.add_argument("--profile-launch", action="store_true",
+                    help="profiling captures: run each pattern's plan for exactly two launches of its "
+                         "depth k (no timing, no JSON line), so ncu can capture the second one")
     ap.add_argument("--tc-engine", default="auto", choices=["auto", "warp", "umma"],
                     help="tensor-core workloads: autotuned engine choice, warp-level MMAs, or tcgen05")
     ap.add_argument("--mma-n", type=int, default=0,
@@ -516,10 +529,21 @@ def main():
     plans, xs, outs = {}, {}, {}
     for p in PATTERNS:
         W = inputs.pattern_weights(p)
-        plans[p] = Plan(N, N, W, tb_depth=args.tb_depth, autotune=not args.no_autotune)
+        plans[p] = Plan(N, N, W, tb_depth=args.tb_depth, threads=args.threads,
+                        autotune=not (args.no_autotune or args.profile_launch))
         xs[p] = torch.from_numpy(inputs.field(N, N)).cuda()
         outs[p] = torch.empty_like(xs[p])
     stream = torch.cuda.current_stream()
+    if args.profile_launch:
+        for p in PATTERNS:
+            k = plans[p].info()["tb_depth"]
+            for _ in range(2):
+                plans[p].run(xs[p], k, out=outs[p])
+            torch.cuda.synchronize()
+            plans[p].status()
+            print(f"profile-launch {p}: 2 launches of k={k} steps, plan {plans[p].info()}")
+            plans[p].close()
+        return 0
 
     def one_step(ev=None):
         for p in PATTERNS:

@@ -304,6 +304,78 @@ void stencil_batch_destroy(stencil_batch_t* batch);
 const char* stencil_batch_last_error(void);
 
 /*
+ * ---- Row slabs: one grid split across ranks ------------------------------------
+ *
+ * The paper splits the grid into tiles with a halo each (Sec. IV-A) and swaps
+ * halos between neighbouring tiles before every step (Sec. IV-B to IV-D).
+ * Here rank p of P owns the rows [y0, y1) of an ny x nx grid (full width) and
+ * keeps G = radius * steps_per_exchange ghost rows above and below them, so
+ * that it can advance steps_per_exchange steps between two exchanges.  Full
+ * rows carry the corner values, so no two-stage corner forwarding is needed.
+ *
+ * The slab buffer (DEVICE, caller-owned, dense row-major) holds buffer_rows x
+ * nx elements: buffer row b is global row y0 - ghost_above + b (mod ny for the
+ * periodic rule).  Under the zero rule a slab at the top (bottom) edge of the
+ * grid has no ghost rows there (ghost_above or ghost_below = 0).
+ *
+ * One temporal block:
+ *   1. exchange: send buffer rows [send_above_row, +G) to the rank above (they
+ *      become its rows [recv_below_row, +G)) and rows [send_below_row, +G) to
+ *      the rank below (its rows [recv_above_row, +G)); receive likewise.  The
+ *      rank above rank p is p-1, the one below p+1, wrapping for periodic.
+ *   2. stencil_slab_step(slab, buf, s, stream), s <= steps_per_exchange:
+ *      afterwards the owned rows hold u_{t+s} exactly (bit-identical to a
+ *      single-domain stencil_run for FP32 storage); ghost rows are stale.
+ * The library does steps 2 only; the exchange is the caller's (NCCL or any
+ * other transport: the rows are contiguous).
+ *
+ * Requirements: every slab with a ghost region owns at least G rows, and
+ * under the zero rule has G rows of neighbours on each side that has ghosts
+ * (otherwise STENCIL_ERR_UNSUPPORTED).
+ */
+typedef struct {
+    int64_t ny, nx;              /* the whole grid                                         */
+    int64_t y0, y1;              /* owned global rows [y0, y1)                             */
+    int radius, boundary;
+    int64_t steps_per_exchange;  /* S                                                      */
+    int64_t ghost_depth;         /* G = radius * S                                         */
+    int64_t ghost_above, ghost_below;  /* G or 0 (zero rule at the grid's top/bottom edge) */
+    int64_t buffer_rows;         /* ghost_above + (y1 - y0) + ghost_below                  */
+    int64_t send_above_row, send_below_row;  /* first buffer row of the G rows sent up / down */
+    int64_t recv_above_row, recv_below_row;  /* first buffer row of the ghost rows received   */
+} stencil_slab_info_t;
+
+typedef struct stencil_slab stencil_slab_t;
+
+/* Geometry of a slab (host only: needs no GPU, allocates nothing). */
+stencil_status_t stencil_slab_geometry(int64_t ny, int64_t nx, int64_t y0, int64_t y1, int radius,
+                                       int boundary, int64_t steps_per_exchange,
+                                       stencil_slab_info_t* info);
+
+/* Create a slab: its geometry and a streaming-kernel plan (FP32 arithmetic,
+ * `dtype` storage) for its buffer, which owns a buffer-sized workspace.
+ * Arguments as for stencil_plan_create; opt may be NULL, opt->kernel must be
+ * AUTO or STREAM and opt->compute AUTO or FP32 (else STENCIL_ERR_UNSUPPORTED). */
+stencil_status_t stencil_slab_create(stencil_slab_t** slab, int64_t ny, int64_t nx, int64_t y0, int64_t y1,
+                                     int radius, const float* weights, int dtype, int boundary,
+                                     int64_t steps_per_exchange, const stencil_options_t* opt);
+
+void stencil_slab_destroy(stencil_slab_t* slab);
+
+stencil_status_t stencil_slab_info(const stencil_slab_t* slab, stencil_slab_info_t* info);
+
+/* The slab's plan (owned by the slab): for stencil_plan_info / stencil_plan_status. */
+stencil_plan_t* stencil_slab_plan(stencil_slab_t* slab);
+
+/* Advance the owned rows of `buf` (DEVICE, buffer_rows x nx, in place) by
+ * `steps` in 0..steps_per_exchange Jacobi steps; the ghost rows must hold the
+ * neighbours' current rows on entry and are stale on return. */
+stencil_status_t stencil_slab_step(stencil_slab_t* slab, void* buf, int64_t steps, stencil_stream_t stream);
+
+/* Message for the last failure of a stencil_slab_* call on the calling thread. */
+const char* stencil_slab_last_error(void);
+
+/*
  * ---- Allocation-free sweep (no counterpart in the paper) ----------------------
  *
  * For callers that must not allocate device memory when they run a sweep: an
@@ -316,11 +388,16 @@ const char* stencil_batch_last_error(void);
  * Same operation and argument meaning as stencil_plan_create + stencil_run,
  * with the library's default configuration (no autotuning).  The ping-pong
  * buffer is a fixed device array of STENCIL_NOALLOC_MAX_BYTES inside the
- * library, reserved on every GPU that loads the library until the process
- * exits.  Grids with ny*nx*element_size above that limit are rejected with
+ * library, kept on every GPU where it was set up until the process exits.
+ * Grids with ny*nx*element_size above that limit are rejected with
  * STENCIL_ERR_UNSUPPORTED (see stencil_noalloc_last_error()).
- *   - The first call on each device looks up the array's device address; make
- *     that first call before any stream capture.
+ *   - The first call on each device (after its arguments pass the checks; a
+ *     call with T == 0 will do) sets the array up: it looks up the array's
+ *     device address and, under CUDA's default lazy module loading, loads the
+ *     module that holds it, which reserves STENCIL_NOALLOC_MAX_BYTES of device
+ *     memory at that moment (STENCIL_ERR_CUDA if that memory is not free).
+ *     Make that first call before any region that must not allocate and
+ *     before any stream capture.  Later calls allocate nothing.
  *   - All calls share the array and it keeps the last call's contents; nothing
  *     in it needs to start at zero.  Calls whose work overlaps on the GPU (two
  *     streams at once, or two threads) race on the array and give wrong results.

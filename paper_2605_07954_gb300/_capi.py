@@ -59,6 +59,16 @@ class stencil_batch_info_t(ctypes.Structure):
                 ("ctas", ctypes.c_int), ("point_steps", ctypes.c_int64)]
 
 
+class stencil_slab_info_t(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int64), ("nx", ctypes.c_int64), ("y0", ctypes.c_int64),
+                ("y1", ctypes.c_int64), ("radius", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("steps_per_exchange", ctypes.c_int64), ("ghost_depth", ctypes.c_int64),
+                ("ghost_above", ctypes.c_int64), ("ghost_below", ctypes.c_int64),
+                ("buffer_rows", ctypes.c_int64), ("send_above_row", ctypes.c_int64),
+                ("send_below_row", ctypes.c_int64), ("recv_above_row", ctypes.c_int64),
+                ("recv_below_row", ctypes.c_int64)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int
@@ -90,6 +100,16 @@ _PROTOS = {
     "stencil_run_noalloc": (_i32, [_i64, _i64, _i32, ctypes.POINTER(ctypes.c_float), _i32, _i32,
                                    _vp, _vp, _i64, _vp]),
     "stencil_noalloc_last_error": (ctypes.c_char_p, []),
+    "stencil_slab_geometry": (_i32, [_i64, _i64, _i64, _i64, _i32, _i32, _i64,
+                                     ctypes.POINTER(stencil_slab_info_t)]),
+    "stencil_slab_create": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _i64, _i32,
+                                   ctypes.POINTER(ctypes.c_float), _i32, _i32, _i64,
+                                   ctypes.POINTER(stencil_options_t)]),
+    "stencil_slab_destroy": (None, [_vp]),
+    "stencil_slab_info": (_i32, [_vp, ctypes.POINTER(stencil_slab_info_t)]),
+    "stencil_slab_plan": (_vp, [_vp]),
+    "stencil_slab_step": (_i32, [_vp, _vp, _i64, _vp]),
+    "stencil_slab_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -134,6 +154,8 @@ class StencilError(RuntimeError):
             msg = lib.stencil_batch_last_error().decode()
         elif "noalloc" in where:
             msg = lib.stencil_noalloc_last_error().decode()
+        elif "slab" in where:
+            msg = lib.stencil_slab_last_error().decode()
         else:
             msg = lib.stencil_last_error().decode()
         super().__init__(f"{where}: {name}: {msg}")

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
         const int ylast = min(y0 + g.by, g.ny);
         // Interior: no masking needed, and the columns the idle threads of the
         // CTA read lie inside the neighbouring tiles' outputs.
-        const bool interior = y0 - R * K >= 0 && ylast + R * K + D <= g.ny && x0 - g.H >= 0 &&
+        const bool interior = y0 - R * K >= 0 && ylast + stream_rows_after(R, K) <= g.ny && x0 - g.H >= 0 &&
                               x0 - g.H + 4 * NT <= g.nx && 4 * NT <= 2 * g.bx + g.H;
         if (g.star) {
             if (interior)

@@ -7,15 +7,21 @@
 // synchronisation is not acceptable.  stencil_plan_create() allocates a
 // ping-pong workspace (and stencil_run() needs a plan), so such callers use
 // this entry point instead.  Its ping-pong buffer is a fixed, file-scope
-// device array that the CUDA driver reserves when the library's module is
-// loaded; every GPU that loads the library keeps it until the process exits.
+// device array of STENCIL_NOALLOC_MAX_BYTES; every GPU that loads it keeps it
+// until the process exits.
 //
 // Only the host code of this file needs the array's device address: on the
 // host, `g_noalloc_scratch` names a host-side stand-in, not device memory, so
 // the address is fetched once per device with cudaGetSymbolAddress (with that
 // device current) and cached.  That set-up happens inside the first call on
-// each device, so the first call on a device should come before any stream
-// capture.
+// each device, after its arguments are checked and before anything else (so a
+// call with T = 0 serves as a warm-up).  Under CUDA's lazy module loading (the
+// default) the set-up is also what loads this file's module, which reserves
+// the array's device memory at that moment: the first call on a device may
+// therefore take up to STENCIL_NOALLOC_MAX_BYTES of device memory (and fail
+// with STENCIL_ERR_CUDA if there is none), so it belongs before any region
+// that must not allocate and before any stream capture.  Later calls take
+// nothing.
 //
 // The array is shared by every call in the process and keeps the contents of
 // the last call.  Nothing in it has to start at zero: each launch writes every
@@ -56,11 +62,16 @@ stencil_status_t nfail(stencil_status_t st, const std::string& msg) {
     return st;
 }
 
+// A failed runtime call also clears the runtime's last-error state (for
+// errors that are not sticky), so the caller's next error check does not
+// report it a second time.
 #define NCK(call)                                                                           \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
+        if (e_ != cudaSuccess) {                                                            \
+            (void)cudaGetLastError();                                                       \
             return nfail(STENCIL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                   \
     } while (0)
 
 // Device address of the scratch array on the current device (set up once).
@@ -160,18 +171,20 @@ stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const f
             if (a != radius && b != radius && v != 0.f) star = 0;
         }
 
+    // Per-device set-up first, so that any call (T = 0 included) does it.
+    void* scratch = nullptr;
+    stencil_status_t s = scratch_address(&scratch);
+    if (s != STENCIL_OK) return s;
+
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)ny * (size_t)nx * elem;
     if (T == 0) {
         if (in != out) NCK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
         return STENCIL_OK;
     }
-    void* scratch = nullptr;
-    stencil_status_t s = scratch_address(&scratch);
-    if (s != STENCIL_OK) return s;
 
     // Fixed configuration: the library's default depth and 128-thread CTAs.
-    const int kdef = radius == 1 ? 8 : (radius == 2 ? 4 : (star ? 4 : 1));
+    const int kdef = radius == 1 ? 8 : (radius == 2 ? 4 : (star ? 2 : 1));
     const int k = depth_at_most(radius, star, kdef);
     Geometry g{};
     g.H = (radius * k + 3) / 4 * 4;
@@ -190,7 +203,8 @@ stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const f
         NCK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r.fn, g.nt, smem));
     }
-    const long long resident = (long long)std::max(per_sm, 1) * sms;
+    if (per_sm < 1) return nfail(STENCIL_ERR_UNSUPPORTED, "streaming kernel does not fit on an SM");
+    const long long resident = (long long)per_sm * sms;
     const long long by_min = std::max(8LL, 4LL * radius * k);
     const long long tiles = std::max(1LL, std::min(std::max(1LL, resident / g.strips), cdiv(ny, by_min)));
     g.by = (int)cdiv(ny, tiles);

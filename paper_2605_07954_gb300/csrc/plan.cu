@@ -150,11 +150,13 @@ static int stream_depth_at_most(int R, int star, int k) {
 
 // Default depth before any tuning: deep enough that HBM stops binding for the
 // light stencils, 1 for the 49-point box (already arithmetic-bound at k = 1).
-// These are the best measured choices for 8192^2 FP32 grids on GB300.
+// These are the best measured choices for 8192^2 FP32 grids on GB300 (the
+// 13-point star: k = 2 at 4 CTAs per SM beats k = 3 and 4, which hold more
+// partial sums per thread and fit fewer CTAs).
 static int default_depth(int R, int star) {
     if (R == 1) return 8;
     if (R == 2) return 4;
-    return star ? 4 : 1;
+    return star ? 2 : 1;
 }
 
 static const int kDefaultThreads = 128;

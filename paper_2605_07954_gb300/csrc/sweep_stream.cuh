@@ -19,13 +19,15 @@
 // level l+1 is produced from level l as a pipeline along y: when row y of
 // level l arrives it is the last contribution to output row y-R of level l+1
 // and the first to row y+R.  A thread keeps 2R+1 partial sums per column and
-// level in registers (a window sliding down the rows); a completed
-// level-(l+1) row feeds level l+2 in the same row step.  Only the R columns
-// next to a thread's 4 columns cross threads: each level publishes its newest
-// row's edge values to a double-buffered shared-memory array (R = 1: separate
-// left/right edge arrays, so every access is conflict-free and unit stride;
-// R = 2, 3: the whole 16-byte chunk), does the products that need only
-// its own columns, waits at one barrier, then adds the products that need the
+// level in registers (a window sliding down the rows).  A completed
+// level-(l+1) row is handed to level l+2 at the NEXT row step, so the K levels
+// of one row step are independent: they share one barrier per row step (not
+// one per level) and their arithmetic interleaves.  Only the R columns next to
+// a thread's 4 columns cross threads: each level publishes its input row's edge
+// values to a double-buffered shared-memory array (R = 1: separate left/right
+// edge arrays, so every access is conflict-free and unit stride; R = 2, 3: the
+// whole 16-byte chunk), does the products that need only its own columns,
+// waits at the row step's barrier, then adds the products that need the
 // neighbours' edges.
 //
 // Input rows stream from HBM into a shared-memory ring with cp.async, PF rows
@@ -44,7 +46,8 @@
 //
 // Summation order: each output accumulates dy = -R .. R as rows arrive; within
 // a row the own-column products come first and the neighbour-column products
-// after the barrier.  Star footprints skip the off-axis (zero) weights.
+// after them, each group in ascending dx.  Star footprints skip the off-axis
+// (zero) weights.  The order depends neither on K nor on the tile shape.
 #pragma once
 
 #include <type_traits>
@@ -70,6 +73,11 @@ __host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// Two scalar FMAs with one weight: the weight comes straight from the constant
+// bank, where a packed FMA needs the (w, w) pair in registers.
+__device__ __forceinline__ float2 sfma2(float w, float2 b, float2 c) {
+    return make_float2(fmaf(w, b.x, c.x), fmaf(w, b.y, c.y));
+}
 
 // Weight sources for the tile body.  ParamWeights reads the (w, w) pairs from
 // the kernel parameters (the constant bank); RegWeights holds a grid's pairs
@@ -150,21 +158,27 @@ __device__ __forceinline__ void load_chunk_scalar(const StreamParams& p, int y, 
 
 // ---- arithmetic -----------------------------------------------------------------
 //
-// Column pairs.  A thread's 4 columns c0..c3 are held as P0 = (c0, c2) and
-// P1 = (c1, c3), and its outputs as A0 = (o0, o2), A1 = (o1, o3).  The weight
-// (dy, dx) then updates pair q from the source pair (c[q+dx], c[q+dx+2]): for
-// q+dx in {0, 1} that is P0 or P1 itself, so every own-column product takes its
-// operands straight from registers; only the pairs that straddle a neighbour's
-// columns are assembled.  A completed output pair is directly the next level's
-// input pair.
+// Column pairs.  Radius 1: a thread's 4 columns c0..c3 are held as
+// Pa = (c0, c2) and Pb = (c1, c3), and its outputs as A0 = (o0, o2),
+// A1 = (o1, o3).  The weight (dy, dx) then updates pair q from the source pair
+// (c[q+dx], c[q+dx+2]): for q+dx in {0, 1} that is Pa or Pb itself, so every
+// own-column product takes its operands straight from registers; only the
+// pairs that straddle a neighbour's columns are assembled.  Radius 2 and 3:
+// adjacent pairs Pa = (c0, c1), Pb = (c2, c3) (measured faster there).  In both
+// layouts a completed output pair is directly the next level's input pair.
+//
+// Weight rows.  Row m = dy + R of the weights multiplies the row that arrives
+// m rows after the first input row of an output.  The products of one arriving
+// row are split by m: rows m >= 1 go into partial sums that hold earlier rows'
+// products already; row m = 0 starts a new partial sum (a multiply, no add).
 
-// Own-column products of one arriving row into the 2R+1 partial sums.
-template <int R, bool STAR, class WS>
-__device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 1][2], float2 P0,
-                                             float2 P1, int j) {
+// Own-column products, weight rows MLO..MHI, radius 1 layout.
+template <int R, bool STAR, int MLO, int MHI, class WS>
+__device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 1][2], float2 Pa,
+                                             float2 Pb, int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
+    for (int m = MLO; m <= MHI; ++m) {
         const int slot = (j - m + R + 2 * D) % D;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -174,7 +188,7 @@ __device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 
                 if (STAR && m != R && dx != 0) continue;
                 const int c = q + dx;
                 if (c != 0 && c != 1) continue;
-                const float2 src = c == 0 ? P0 : P1;
+                const float2 src = c == 0 ? Pa : Pb;
                 if (first) {
                     acc[slot][q] = fmul2(wgt2<R>(p, m, dx), src);
                     first = false;
@@ -186,14 +200,15 @@ __device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 
     }
 }
 
-// Products whose source pair straddles a neighbour column.  col(j) is column
-// j of the extended row, j in [-R, 4+R): left halo, own, right halo.
-template <int R, bool STAR, class WS, class COL>
+// Products whose source pair straddles a neighbour column, weight rows
+// MLO..MHI, radius 1 layout.  col.pair(c) = (column c, column c + 2) of the
+// extended row (left halo, own, right halo).
+template <int R, bool STAR, int MLO, int MHI, class WS, class COL>
 __device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R + 1][2], const COL& col,
                                               int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
+    for (int m = MLO; m <= MHI; ++m) {
         if (STAR && m != R) continue;
         const int slot = (j - m + R + 2 * D) % D;
 #pragma unroll
@@ -208,16 +223,15 @@ __device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R +
     }
 }
 
-// Adjacent pairing (used for R >= 2, where it measures faster): pairs
-// (c0, c1), (c2, c3), outputs (o0, o1), (o2, o3); the source of weight
-// (dy, dx) for pair q is (c[2q+dx], c[2q+dx+1]).  cur2 = {(c0,c1), (c2,c3)},
-// mid = (c1, c2); ext[i] = column i - R.
-template <int R, bool STAR, class WS>
-__device__ __forceinline__ void own_products_adj(const WS& p, float2 (&acc)[2 * R + 1][2],
-                                                 const float2 (&cur2)[2], float2 mid, int j) {
+// Adjacent layout (radius 2, 3): the source of weight (dy, dx) for output pair
+// q is (c[2q+dx], c[2q+dx+1]); own pairs are Pa = (c0,c1), Pb = (c2,c3) and
+// mid = (c1, c2).
+template <int R, bool STAR, int MLO, int MHI, class WS>
+__device__ __forceinline__ void own_products_adj(const WS& p, float2 (&acc)[2 * R + 1][2], float2 Pa,
+                                                 float2 Pb, float2 mid, int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
+    for (int m = MLO; m <= MHI; ++m) {
         const int slot = (j - m + R + 2 * D) % D;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -227,7 +241,13 @@ __device__ __forceinline__ void own_products_adj(const WS& p, float2 (&acc)[2 * 
                 if (STAR && m != R && dx != 0) continue;
                 const int c = 2 * q + dx;
                 if (c < 0 || c + 1 > 3) continue;
-                const float2 src = (c == 0) ? cur2[0] : (c == 2 ? cur2[1] : mid);
+                const float2 src = (c == 0) ? Pa : (c == 2 ? Pb : mid);
+                if (STAR && R == 3 && m == R && !first) {
+                    // radius-3 star, centre row: scalar FMAs keep these seven
+                    // weights out of the register file (measured faster)
+                    acc[slot][q] = sfma2(wgt2<R>(p, m, dx).x, src, acc[slot][q]);
+                    continue;
+                }
                 if (first) {
                     acc[slot][q] = fmul2(wgt2<R>(p, m, dx), src);
                     first = false;
@@ -239,12 +259,14 @@ __device__ __forceinline__ void own_products_adj(const WS& p, float2 (&acc)[2 * 
     }
 }
 
-template <int R, bool STAR, class WS>
+// Halo products, adjacent layout, general footprint: ext[i] = column i - R of
+// the extended row.
+template <int R, bool STAR, int MLO, int MHI, class WS>
 __device__ __forceinline__ void halo_products_adj(const WS& p, float2 (&acc)[2 * R + 1][2],
                                                   const float (&ext)[4 + 2 * R], int j) {
     constexpr int D = 2 * R + 1;
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
+    for (int m = MLO; m <= MHI; ++m) {
         if (STAR && m != R) continue;
         const int slot = (j - m + R + 2 * D) % D;
 #pragma unroll
@@ -260,18 +282,51 @@ __device__ __forceinline__ void halo_products_adj(const WS& p, float2 (&acc)[2 *
     }
 }
 
+// Halo products of the radius-3 star (only weight row m = 3 reaches across
+// columns).  lft = columns -4..-1, rgt = columns 4..7 as loaded from shared
+// memory.  Every product runs as a scalar FMA with its weight from the
+// constant bank: no pair has to be assembled first and no weight pair has to
+// be held in registers.  Per output the products are added in ascending dx,
+// the order halo_products_adj uses.
+template <class WS>
+__device__ __forceinline__ void halo_products_star3(const WS& p, float2 (&acc)[7][2], float4 lft,
+                                                    float4 rgt, float2 Pa, float2 Pb, int j) {
+    const int slot = (j - 3 + 3 + 14) % 7;
+    float2 A0 = acc[slot][0], A1 = acc[slot][1];
+    const float wm3 = wgt2<3>(p, 3, -3).x, wm1 = wgt2<3>(p, 3, -1).x;
+    const float w1 = wgt2<3>(p, 3, 1).x, w3 = wgt2<3>(p, 3, 3).x;
+    // outputs (o0, o1): dx = -3, -2, -1, 3
+    A0.x = fmaf(wm3, lft.y, A0.x);
+    A0.y = fmaf(wm3, lft.z, A0.y);
+    A0 = sfma2(wgt2<3>(p, 3, -2).x, make_float2(lft.z, lft.w), A0);
+    A0.x = fmaf(wm1, lft.w, A0.x);
+    A0.y = fmaf(wm1, Pa.x, A0.y);
+    A0.x = fmaf(w3, Pb.y, A0.x);
+    A0.y = fmaf(w3, rgt.x, A0.y);
+    // outputs (o2, o3): dx = -3, 1, 2, 3
+    A1.x = fmaf(wm3, lft.w, A1.x);
+    A1.y = fmaf(wm3, Pa.x, A1.y);
+    A1.x = fmaf(w1, Pb.y, A1.x);
+    A1.y = fmaf(w1, rgt.x, A1.y);
+    A1 = sfma2(wgt2<3>(p, 3, 2).x, make_float2(rgt.x, rgt.y), A1);
+    A1.x = fmaf(w3, rgt.y, A1.x);
+    A1.y = fmaf(w3, rgt.z, A1.y);
+    acc[slot][0] = A0;
+    acc[slot][1] = A1;
+}
+
 // The extended row of one level-row for R = 1: own pairs plus the
 // neighbours' edge columns hl (column -1) and hr (column 4).
 template <int R>
 struct ExtRow {
-    float2 P0, P1;
+    float2 Pa, Pb;
     float hl, hr;
     __device__ __forceinline__ float at(int j) const {
         switch (j) {
-            case 0: return P0.x;
-            case 1: return P1.x;
-            case 2: return P0.y;
-            case 3: return P1.y;
+            case 0: return Pa.x;
+            case 1: return Pb.x;
+            case 2: return Pa.y;
+            case 3: return Pb.y;
         }
         return j < 0 ? hl : hr;
     }
@@ -279,10 +334,40 @@ struct ExtRow {
     __device__ __forceinline__ float2 pair(int c) const { return make_float2(at(c), at(c + 2)); }
 };
 
+// Level schedule (see stream_tile): radius 1 forwards a completed row to the
+// next level in the same row step; radius 2 and 3 hand it over one row step
+// later (measured faster for each: the hand-over frees the K levels of a row
+// step from one another but keeps more values live, which costs radius 1's
+// deep blocks more occupancy than it gains).
+__host__ __device__ constexpr bool stream_handover(int R) { return R >= 2; }
+
+// Input rows a tile's row loop may load beyond its last output row: R*K for
+// the halo, K-1 for the hand-over between levels (radius 2, 3), D-1 for
+// rounding the loop up to its unroll.  A tile whose rows
+// [y0 - R*K, ylast + stream_rows_after) lie in the grid needs no row bounds
+// checks.
+__host__ __device__ constexpr int stream_rows_after(int R, int K) {
+    return R * K + (stream_handover(R) ? K : 0) + 2 * R + 1;
+}
+
 // One CTA's tile.  EDGE = the tile loads rows or columns outside the grid:
 // loads are bounds-checked (zero rule) or wrapped (periodic), and with the
 // zero rule every level's out-of-grid values are forced to 0.  Interior tiles
 // run without any of that.
+//
+// Schedule.  Level l (l = 0 .. K-1) turns time level l into l+1; level 0 takes
+// input row ybeg + s at row step s.  Radius 1 (same-step forwarding): level
+// l >= 1 takes the row that level l-1 completes in the same step, after one
+// barrier per level.  Radius 2, 3 (hand-over): level l >= 1 takes the row that
+// level l-1 completed at step s-1, so the K levels of one row step do not
+// depend on one another and share ONE barrier: (A) every level publishes its input row's edge
+// columns and adds its own-column products of weight rows 1..2R; barrier;
+// (B) from the top level down, every level adds its halo products, then starts
+// the partial sum of weight row 0 in the slot its completed row was handed over
+// from (the level above has consumed it by then), masks its newly completed
+// row (zero rule, edge tiles) and, at the top level, stores it.  Per output the
+// products are still added row by row (dy = -R .. R), own columns before
+// neighbour columns, so the result does not depend on the schedule or on K.
 template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, class WS>
 __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws, char* ring,
                                             float* ebuf, int NT, int tid, int x0, int y0) {
@@ -310,8 +395,11 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
 #pragma unroll
         for (int m = 0; m < D; ++m) acc[l][m][0] = acc[l][m][1] = make_float2(0.f, 0.f);
 
-    const int nreal = (ylast - y0) + 2 * R * K;  // row steps that matter
-    const int nsteps = (nreal + D - 1) / D * D;  // rounded up to the unroll
+    // Level K-1 completes output row ybeg + s - (K-1)(R+1) - R at step s with
+    // the hand-over, ybeg + s - K*R without.
+    constexpr int HAND = stream_handover(R) ? 1 : 0;
+    const int nreal = (ylast - y0) + 2 * R * K + HAND * (K - 1);  // row steps that matter
+    const int nsteps = (nreal + D - 1) / D * D;            // rounded up to the unroll
 
     // VEC: the chunk this thread copies for row y.
     const TS* gin = static_cast<const TS*>(p.in);
@@ -354,7 +442,9 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const int s = s0 + j;
-            float cur[4];
+            const int cin = (j + R) % D;        // slot completed at the previous step
+            const int cdone = (j + R + 1) % D;  // slot completed at this step
+            float cur[4];                       // level 0's input row
             if constexpr (VEC) {
                 issue_row(s + PF - 1);
                 cp_async_wait<PF - 1>();
@@ -365,91 +455,155 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                 if (s + 2 < nsteps) load_chunk_scalar<TS>(p, ybeg + s + 2, c0, active, nreg1);
             }
             float* bpar = ebuf + (s & 1) * SZ;
-            if constexpr (R == 1) {
-                // (c0, c2) / (c1, c3) pairs; edges through two scalar arrays.
-                float2 P0 = make_float2(cur[0], cur[2]), P1 = make_float2(cur[1], cur[3]);
+            if constexpr (!HAND) {
+                // Same-step forwarding (radius 1): level l's completed row is
+                // level l+1's input row of this step; one barrier per level.
+                float2 Pa = make_float2(cur[0], cur[2]), Pb = make_float2(cur[1], cur[3]);
 #pragma unroll
                 for (int l = 0; l < K; ++l) {
-                    // Level l's row ybeg - l*R + s arrives; it feeds level l+1.
                     float* B = bpar + 2 * l * SZ;
-                    B[tid + 1] = P0.x;                          // column 0
-                    B[kStreamMaxThreads + 2 + tid + 1] = P1.y;  // column 3
-                    own_products<R, STAR>(ws, acc[l], P0, P1, j);
+                    B[tid + 1] = Pa.x;                          // column 0
+                    B[kStreamMaxThreads + 2 + tid + 1] = Pb.y;  // column 3
+                    own_products<R, STAR, 0, 2 * R>(ws, acc[l], Pa, Pb, j);
                     __syncthreads();
                     ExtRow<R> ext;
-                    ext.P0 = P0;
-                    ext.P1 = P1;
+                    ext.Pa = Pa;
+                    ext.Pb = Pb;
                     ext.hl = B[kStreamMaxThreads + 2 + tid];
                     ext.hr = B[tid + 2];
-                    halo_products<R, STAR>(ws, acc[l], ext, j);
+                    halo_products<R, STAR, 0, 2 * R>(ws, acc[l], ext, j);
                     // Output row (arriving row) - R of level l+1 is complete.
-                    const int cs = (j + R + 1) % D;
-                    P0 = acc[l][cs][0];
-                    P1 = acc[l][cs][1];
+                    Pa = acc[l][cdone][0];
+                    Pb = acc[l][cdone][1];
                     if constexpr (EDGE) {
                         if (mask) {
                             const int yo = ybeg - (l + 1) * R + s;
                             const bool row_out = yo < 0 || yo >= ny;
-                            if (row_out || !col_in[0]) P0.x = 0.f;
-                            if (row_out || !col_in[2]) P0.y = 0.f;
-                            if (row_out || !col_in[1]) P1.x = 0.f;
-                            if (row_out || !col_in[3]) P1.y = 0.f;
+                            if (row_out || !col_in[0]) Pa.x = 0.f;
+                            if (row_out || !col_in[2]) Pa.y = 0.f;
+                            if (row_out || !col_in[1]) Pb.x = 0.f;
+                            if (row_out || !col_in[3]) Pb.y = 0.f;
                         }
                     }
                 }
-                cur[0] = P0.x;
-                cur[1] = P1.x;
-                cur[2] = P0.y;
-                cur[3] = P1.y;
+                const int yo = ybeg - R * K + s;
+                if (store_chunk && yo >= y0 && yo < ylast) {
+                    TS* orow = static_cast<TS*>(p.out) + (size_t)yo * ld;
+                    const float4 o = make_float4(Pa.x, Pb.x, Pa.y, Pb.y);
+                    if (VEC) {
+                        Storage<TS>::store4(orow + c0, o);
+                    } else {
+                        const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (c0 + e < nx) Storage<TS>::store1(orow + c0 + e, ov[e]);
+                    }
+                }
             } else {
-                // (c0, c1) / (c2, c3) pairs; edges through the whole 16-byte chunk.
+            // Hand-over (radius 2, 3).  The input pairs of level l at this step.
+            auto level_in = [&](int l, float2& Pa, float2& Pb) {
+                if (l == 0) {
+                    if constexpr (R == 1) {
+                        Pa = make_float2(cur[0], cur[2]);
+                        Pb = make_float2(cur[1], cur[3]);
+                    } else {
+                        Pa = make_float2(cur[0], cur[1]);
+                        Pb = make_float2(cur[2], cur[3]);
+                    }
+                } else {
+                    Pa = acc[l - 1][cin][0];
+                    Pb = acc[l - 1][cin][1];
+                }
+            };
+            // (A) publish edges, own-column products of weight rows 1..2R.
 #pragma unroll
-                for (int l = 0; l < K; ++l) {
-                    float* B = bpar + 2 * l * SZ;
-                    reinterpret_cast<float4*>(B)[tid + 1] = make_float4(cur[0], cur[1], cur[2], cur[3]);
-                    const float2 cur2[2] = {make_float2(cur[0], cur[1]), make_float2(cur[2], cur[3])};
-                    own_products_adj<R, STAR>(ws, acc[l], cur2, make_float2(cur[1], cur[2]), j);
-                    __syncthreads();
-                    float ext[4 + 2 * R];
+            for (int l = 0; l < K; ++l) {
+                float* B = bpar + 2 * l * SZ;
+                float2 Pa, Pb;
+                level_in(l, Pa, Pb);
+                if constexpr (R == 1) {
+                    B[tid + 1] = Pa.x;                          // column 0
+                    B[kStreamMaxThreads + 2 + tid + 1] = Pb.y;  // column 3
+                    own_products<R, STAR, 1, 2 * R>(ws, acc[l], Pa, Pb, j);
+                } else {
+                    reinterpret_cast<float4*>(B)[tid + 1] = make_float4(Pa.x, Pa.y, Pb.x, Pb.y);
+                    own_products_adj<R, STAR, 1, 2 * R>(ws, acc[l], Pa, Pb, make_float2(Pa.y, Pb.x), j);
+                }
+            }
+            __syncthreads();
+            // (B) top level first: halo products, weight row 0, mask, store.
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) ext[R + e] = cur[e];
+            for (int l = K - 1; l >= 0; --l) {
+                const float* B = bpar + 2 * l * SZ;
+                float2 Pa, Pb;
+                level_in(l, Pa, Pb);
+                if constexpr (R == 1) {
+                    ExtRow<R> ext;
+                    ext.Pa = Pa;
+                    ext.Pb = Pb;
+                    ext.hl = B[kStreamMaxThreads + 2 + tid];
+                    ext.hr = B[tid + 2];
+                    halo_products<R, STAR, 1, 2 * R>(ws, acc[l], ext, j);
+                    own_products<R, STAR, 0, 0>(ws, acc[l], Pa, Pb, j);
+                    halo_products<R, STAR, 0, 0>(ws, acc[l], ext, j);
+                } else {
                     const float4 a = reinterpret_cast<const float4*>(B)[tid];
                     const float4 b = reinterpret_cast<const float4*>(B)[tid + 2];
-                    const float lft[4] = {a.x, a.y, a.z, a.w}, rgt[4] = {b.x, b.y, b.z, b.w};
+                    if constexpr (STAR && R == 3) {
+                        halo_products_star3(ws, acc[l], a, b, Pa, Pb, j);
+                        own_products_adj<R, STAR, 0, 0>(ws, acc[l], Pa, Pb, make_float2(Pa.y, Pb.x), j);
+                    } else {
+                        float ext[4 + 2 * R];
+                        ext[R + 0] = Pa.x;
+                        ext[R + 1] = Pa.y;
+                        ext[R + 2] = Pb.x;
+                        ext[R + 3] = Pb.y;
+                        const float lft[4] = {a.x, a.y, a.z, a.w}, rgt[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                    for (int i = 0; i < R; ++i) {
-                        ext[i] = lft[4 - R + i];
-                        ext[R + 4 + i] = rgt[i];
+                        for (int i = 0; i < R; ++i) {
+                            ext[i] = lft[4 - R + i];
+                            ext[R + 4 + i] = rgt[i];
+                        }
+                        halo_products_adj<R, STAR, 1, 2 * R>(ws, acc[l], ext, j);
+                        own_products_adj<R, STAR, 0, 0>(ws, acc[l], Pa, Pb, make_float2(Pa.y, Pb.x), j);
+                        halo_products_adj<R, STAR, 0, 0>(ws, acc[l], ext, j);
                     }
-                    halo_products_adj<R, STAR>(ws, acc[l], ext, j);
-                    const int cs = (j + R + 1) % D;
-                    cur[0] = acc[l][cs][0].x;
-                    cur[1] = acc[l][cs][0].y;
-                    cur[2] = acc[l][cs][1].x;
-                    cur[3] = acc[l][cs][1].y;
-                    if constexpr (EDGE) {
-                        if (mask) {
-                            const int yo = ybeg - (l + 1) * R + s;
-                            const bool row_out = yo < 0 || yo >= ny;
+                }
+                // acc[l][cdone] is level l+1's row ybeg + s - l(R+1) - R, complete.
+                if constexpr (EDGE) {
+                    if (mask) {
+                        const int yo = ybeg + s - l * (R + 1) - R;
+                        const bool row_out = yo < 0 || yo >= ny;
+                        float2& A0 = acc[l][cdone][0];
+                        float2& A1 = acc[l][cdone][1];
+                        // element e of the chunk: R == 1 (A0.x, A1.x, A0.y, A1.y),
+                        // else (A0.x, A0.y, A1.x, A1.y)
+                        constexpr int e_a0y = R == 1 ? 2 : 1, e_a1x = R == 1 ? 1 : 2;
+                        if (row_out || !col_in[0]) A0.x = 0.f;
+                        if (row_out || !col_in[e_a0y]) A0.y = 0.f;
+                        if (row_out || !col_in[e_a1x]) A1.x = 0.f;
+                        if (row_out || !col_in[3]) A1.y = 0.f;
+                    }
+                }
+                if (l == K - 1) {
+                    const int yo = ybeg + s - (K - 1) * (R + 1) - R;
+                    if (store_chunk && yo >= y0 && yo < ylast) {
+                        const float2 A0 = acc[l][cdone][0], A1 = acc[l][cdone][1];
+                        const float4 o = R == 1 ? make_float4(A0.x, A1.x, A0.y, A1.y)
+                                                : make_float4(A0.x, A0.y, A1.x, A1.y);
+                        TS* orow = static_cast<TS*>(p.out) + (size_t)yo * ld;
+                        if (VEC) {
+                            Storage<TS>::store4(orow + c0, o);
+                        } else {
+                            const float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
                             for (int e = 0; e < 4; ++e)
-                                if (row_out || !col_in[e]) cur[e] = 0.f;
+                                if (c0 + e < nx) Storage<TS>::store1(orow + c0 + e, ov[e]);
                         }
                     }
                 }
             }
-            // cur holds level K's row ybeg - K*R + s.
-            const int yo = ybeg - R * K + s;
-            if (store_chunk && yo >= y0 && yo < ylast) {
-                TS* orow = static_cast<TS*>(p.out) + (size_t)yo * ld;
-                if (VEC) {
-                    Storage<TS>::store4(orow + c0, make_float4(cur[0], cur[1], cur[2], cur[3]));
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (c0 + e < nx) Storage<TS>::store1(orow + c0 + e, cur[e]);
-                }
-            }
+            }  // hand-over
         }
     }
     if constexpr (VEC) cp_async_wait<0>();
@@ -458,7 +612,6 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
 template <int R, bool STAR, int K, typename TS, bool VEC>
 __global__ void __launch_bounds__(kStreamMaxThreads)
     sweep_stream_kernel(const __grid_constant__ StreamParams p) {
-    constexpr int D = 2 * R + 1;
     constexpr int PF = kStreamPrefetch;
     constexpr int CB = 4 * (int)sizeof(TS);
     extern __shared__ float4 smem_f4[];
@@ -478,8 +631,8 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
     // row loop) and every column of its strip lies inside the grid.
     const int ny = (int)p.ny, nx = (int)p.nx;
     const int ylast = min(y0 + p.by, ny);
-    const bool interior = VEC && y0 - R * K >= 0 && ylast + R * K + D <= ny && x0 - p.H >= 0 &&
-                          x0 - p.H + 4 * NT <= nx;
+    const bool interior = VEC && y0 - R * K >= 0 && ylast + stream_rows_after(R, K) <= ny &&
+                          x0 - p.H >= 0 && x0 - p.H + 4 * NT <= nx;
     const ParamWeights ws{p};
     if (interior)
         stream_tile<R, STAR, K, TS, VEC, false>(p, ws, ring, ebuf, NT, tid, x0, y0);

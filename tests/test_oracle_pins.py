@@ -132,6 +132,40 @@ def test_dyadic_exact(oracle, r, T):
         assert np.array_equal(got32.astype(np.float64), want3)
 
 
+def _int_sweep_periodic(u, Wi, T, r):
+    """Exact integer T-step correlation with wrapped indices (Python ints, np.roll)."""
+    u = u.astype(object)
+    for _ in range(T):
+        v = np.zeros(u.shape, dtype=object)
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                # v[i][j] += W[dy][dx] * u[(i+dy) mod ny][(j+dx) mod nx]
+                v = v + int(Wi[dy + r, dx + r]) * np.roll(u, (-dy, -dx), axis=(0, 1))
+        u = v
+    return u
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_dyadic_exact_periodic_fp32(oracle, r):
+    """The FP32 oracle under the periodic rule: dyadic data, exact integer reference.
+
+    Weights k/8 with |k| <= 2 and inputs m/256, m < 256: after T steps every
+    value is an integer over 8^T * 256 of magnitude <= (2 (2r+1)^2)^T * 255,
+    which needs at most 24 bits for T = 2 at r = 2 (50^2 * 255 < 2^20) and T = 3
+    at r = 1 (18^3 * 255 < 2^21), so FP32 is exact and must agree bit for bit."""
+    rng = np.random.default_rng(12 + r)
+    d = 2 * r + 1
+    Wi = rng.integers(-2, 3, size=(d, d))
+    ui = rng.integers(0, 256, size=(9, 13))
+    T = 3 if r == 1 else 2
+    exact = _int_sweep_periodic(ui, Wi, T, r)
+    want = np.array([[float(v) / (8 ** T * 256) for v in row] for row in exact])
+    got32 = oracle.sweep_f32((ui / 256.0).astype(np.float32), (Wi / 8.0).astype(np.float32), T, "periodic")
+    assert np.array_equal(got32.astype(np.float64), want)
+    got64 = oracle.sweep_f64(ui / 256.0, Wi / 8.0, T, "periodic")
+    assert np.array_equal(got64, want)
+
+
 @pytest.mark.parametrize("name", ["heat5", "box9", "star13", "box49", "asym"])
 def test_fourier_mode_periodic(oracle, name):
     """u_0 = cos(theta) decays as |lam|^T cos(theta + T arg lam), lam = sum W e^{i phase}."""
@@ -234,6 +268,18 @@ def test_light_cone(oracle):
     sub = u0[y0 - m:y1 + m, x0 - m:x1 + m]
     win = oracle.sweep_f64(sub, W, T)[m:-m, m:-m]
     np.testing.assert_allclose(win, full[y0:y1, x0:x1], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,ny,nx,T,win,chunk", [
+    ("box9", 120, 140, 37, 16, 5), ("star13", 200, 90, 23, 8, 7), ("box49", 60, 60, 9, 12, 4),
+    ("asym", 80, 75, 11, 10, 3)])
+def test_corner_window_is_the_light_cone(oracle, name, ny, nx, T, win, chunk):
+    """corner_window_f64 (the shrinking light cone) equals the corner of a
+    whole-grid sweep bit for bit, including grids narrower than the cone."""
+    W = _asym_weights(2, seed=3) * 0.2 if name == "asym" else inputs.pattern_weights(name)
+    u0 = inputs.field(ny, nx)
+    full = oracle.sweep_f64(u0, W, T)[:win, :win]
+    assert np.array_equal(oracle.corner_window_f64(u0, W, T, win, chunk), full)
 
 
 def test_linearity_and_transpose(oracle):

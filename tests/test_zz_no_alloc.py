@@ -6,6 +6,11 @@ cannot afford cudaMalloc's device-wide synchronisation) get the same sweep as
 stencil_plan_create + stencil_run, using a fixed scratch array inside the
 library instead of a plan's workspace.  This file runs last so that a failure
 here never hides the result of any other test.
+
+Device memory is measured with cudaMemGetInfo around the calls.  The first
+call on a device may take up to STENCIL_NOALLOC_MAX_BYTES (under CUDA's lazy
+module loading it loads the module that holds the scratch array); every later
+call takes nothing.
 """
 import ctypes
 
@@ -18,6 +23,9 @@ from _util import fp32_tol, rel_l2
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+MAX_BYTES = 64 << 20  # STENCIL_NOALLOC_MAX_BYTES
+DT = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
 
 
 @pytest.fixture(scope="module")
@@ -33,44 +41,77 @@ def _noalloc(lib, x, W, T, boundary=0, out=None):
     out = torch.empty_like(x) if out is None else out
     Wc = np.ascontiguousarray(W, dtype=np.float32)
     st = lib.stencil_run_noalloc(x.shape[0], x.shape[1], W.shape[0] // 2,
-                                 Wc.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0, boundary,
-                                 x.data_ptr(), out.data_ptr(), T,
+                                 Wc.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), DT[x.dtype],
+                                 boundary, x.data_ptr(), out.data_ptr(), T,
                                  torch.cuda.current_stream().cuda_stream)
     assert st == 0, lib.stencil_noalloc_last_error().decode()
     return out
 
 
-def _planned(x, W, T, boundary="zero"):
+def _planned(x, W, T, boundary="zero", **opts):
     from paper_2605_07954_gb300 import Plan
-    p = Plan(x.shape[0], x.shape[1], W, boundary=boundary)
+    dt = {torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16"}[x.dtype]
+    p = Plan(x.shape[0], x.shape[1], W, dtype=dt, boundary=boundary, **opts)
     y = p.run(x, T)
     torch.cuda.synchronize()
     p.close()
     return y
 
 
-def test_noalloc_matches_planned_run_twice(lib):
+def _free():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_first_call_sets_up_the_scratch(lib):
+    """A T = 0 call is the per-device warm-up: it copies in to out and takes at
+    most the documented scratch size of device memory; a second one takes none."""
+    x = torch.from_numpy(inputs.field(64, 96)).cuda()
+    y = torch.empty_like(x)
+    free0 = _free()
+    _noalloc(lib, x, inputs.pattern_weights("box9"), 0, out=y)
+    free1 = _free()
+    assert torch.equal(x, y)
+    assert 0 <= free0 - free1 <= MAX_BYTES + (8 << 20), (free0, free1)
+    _noalloc(lib, x, inputs.pattern_weights("box9"), 0, out=y)
+    assert _free() >= free1
+
+
+def test_noalloc_matches_oracle_and_planned_run_twice(lib, oracle):
     """Two calls in a row (different shapes, weights and boundaries) agree with
-    the plan-based path, and the second call allocates no device memory."""
-    cases = [("box9", 2048, 1536, 100, 0), ("star13", 1000, 1204, 37, 1)]
-    free_after = []
+    the FP64 oracle and with the plan-based path, and neither call allocates
+    device memory (the output tensor is allocated by the test beforehand)."""
+    cases = [("box9", 1024, 1536, 100, 0), ("star13", 1000, 1204, 37, 1)]
     for name, ny, nx, T, boundary in cases:
         W = inputs.pattern_weights(name)
-        x = torch.from_numpy(inputs.field(ny, nx)).cuda()
-        ref = _planned(x, W, T, "periodic" if boundary else "zero")
-        torch.cuda.synchronize()
-        free0 = torch.cuda.mem_get_info()[0]
-        y = _noalloc(lib, x, W, T, boundary)
-        torch.cuda.synchronize()
-        free_after.append((free0, torch.cuda.mem_get_info()[0]))
-        assert rel_l2(y.cpu().numpy(), ref.cpu().numpy()) <= fp32_tol(T), name
-    # The call itself took no device memory (the output tensor was allocated
-    # by the test before the call).
-    free0, free1 = free_after[1]
-    assert free1 >= free0
+        u0 = inputs.field(ny, nx)
+        x = torch.from_numpy(u0).cuda()
+        bname = "periodic" if boundary else "zero"
+        ref = _planned(x, W, T, bname)
+        out = torch.empty_like(x)
+        free0 = _free()
+        y = _noalloc(lib, x, W, T, boundary, out=out)
+        assert _free() >= free0, name
+        got = y.cpu().numpy()
+        assert rel_l2(got, ref.cpu().numpy()) <= fp32_tol(T), name
+        assert rel_l2(got, oracle.sweep_f64(u0, W, T, bname)) <= fp32_tol(T), name
 
 
-def test_noalloc_in_place_and_zero_steps(lib):
+def test_noalloc_bf16_storage(lib, oracle):
+    """BF16 storage: bit-identical to the streaming plan with the same depth and
+    CTA size, and within the BF16 gate of the FP64 oracle."""
+    W = inputs.pattern_weights("box9")
+    u0 = inputs.field(512, 768)
+    x = torch.from_numpy(u0).to(torch.bfloat16).cuda()
+    T = 50
+    ref = _planned(x, W, T, kernel="stream", tb_depth=8, threads=128)
+    y = _noalloc(lib, x, W, T)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    assert rel_l2(y.float().cpu().numpy(), oracle.sweep_f64(u0, W, T)) <= 1e-2
+
+
+def test_noalloc_in_place_and_zero_steps(lib, oracle):
     W = inputs.pattern_weights("box9")
     x = torch.from_numpy(inputs.field(257, 300)).cuda()
     ref = _planned(x, W, 13)
@@ -81,6 +122,20 @@ def test_noalloc_in_place_and_zero_steps(lib):
     y = _noalloc(lib, x, W, 0)
     torch.cuda.synchronize()
     assert torch.equal(x, y)
+
+
+def test_noalloc_in_place_staging_path(lib, oracle):
+    """Box-49 runs one step per launch, so in == out with an odd T cannot be
+    split into an even number of launches: the input is staged in the scratch
+    array first.  The result still matches the oracle."""
+    W = inputs.pattern_weights("box49")
+    u0 = inputs.field(300, 400)
+    z = torch.from_numpy(u0).cuda()
+    T = 5
+    free0 = _free()
+    _noalloc(lib, z, W, T, out=z)
+    assert _free() >= free0
+    assert rel_l2(z.cpu().numpy(), oracle.sweep_f64(u0, W, T)) <= fp32_tol(T)
 
 
 def test_noalloc_rejects_grids_beyond_the_scratch(lib):
