@@ -162,20 +162,74 @@ def window_error(got, ref) -> dict:
             "relLinf": float(np.abs(got - ref).max() / np.abs(ref).max())}
 
 
-def cpu_oracle_sample(steps_per_pattern: int = 40, n: int = N):
-    """The FP32 oracle, as it stands, on n x n grids for a few steps of each pattern."""
+_WINDOWS = None
+
+
+def stored_window(key: str):
+    """FP64 oracle values for a benchmark workload (tests/golden/bench_windows.json,
+    written by tests/golden/make_bench_windows.py; bench.py does not run the oracle
+    for these checks)."""
+    global _WINDOWS
+    if _WINDOWS is None:
+        with open(os.path.join(ROOT, "tests", "golden", "bench_windows.json")) as f:
+            _WINDOWS = json.load(f)
+    return _WINDOWS["workloads"].get(key)
+
+
+def check_output(out, key: str, gate: float) -> dict:
+    """Compare the top-left window of a device result with its stored FP64 values."""
+    rec = stored_window(key)
+    if rec is None:
+        return {"checked": False, "why": f"no stored window {key}"}
+    ref = np.asarray(rec["window"], dtype=np.float64)
+    w = ref.shape[0]
+    got = out[:w, :w].float().cpu().numpy()
+    e = window_error(got, ref)
+    e.update({"window": f"top-left {w}x{w} of u_T vs FP64 oracle (light cone)", "gate_relL2": gate,
+              "ok": e["relL2"] <= gate})
+    return e
+
+
+def cpu_oracle_sample(steps_per_pattern: int = 10, n: int = N, repeats: int = 3):
+    """The FP32 oracle, as it stands, on n x n grids for a few steps of each
+    pattern: best of `repeats` runs, all host threads."""
     import oracle
     from paper_2605_07954_gb300 import inputs
     oracle.build()
     fields = {p: inputs.field(n, n) for p in PATTERNS}
     ws = {p: inputs.pattern_weights(p) for p in PATTERNS}
-    t0 = time.perf_counter()
-    for p in PATTERNS:
-        oracle.sweep_f32(fields[p], ws[p], steps_per_pattern)
-    dt = time.perf_counter() - t0
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        for p in PATTERNS:
+            oracle.sweep_f32(fields[p], ws[p], steps_per_pattern)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
     updates = len(PATTERNS) * n * n * steps_per_pattern
-    return updates / dt / 1e9, dt, oracle.num_threads(), \
-        f"FP32 oracle, {len(PATTERNS)} patterns x {n}x{n} x {steps_per_pattern} steps"
+    return updates / best / 1e9, best, oracle.num_threads(), \
+        f"FP32 oracle, {len(PATTERNS)} patterns x {n}x{n} x {steps_per_pattern} steps, best of {repeats}"
+
+
+def cpu_heat512_single_thread(repeats: int = 3) -> dict:
+    """The FP32 oracle on the Heat 512^2 x 100 workload with one host thread (best of 3)."""
+    import oracle
+    from paper_2605_07954_gb300 import inputs
+    oracle.build()
+    u0, W = inputs.field(512, 512), inputs.pattern_weights("heat5")
+    n0 = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        best = min(_timed(lambda: oracle.sweep_f32(u0, W, 100)) for _ in range(repeats))
+    finally:
+        oracle.set_num_threads(n0)
+    return {"value": 512 * 512 * 100 / best / 1e9, "unit": "GStencil/s", "cores": 1, "seconds": best,
+            "sample": "FP32 oracle, Heat 512x512 x 100 steps, 1 thread, best of 3"}
+
+
+def _timed(fn) -> float:
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
 
 
 def run_reference(args):
@@ -184,7 +238,7 @@ def run_reference(args):
         return 0
     vals = []
     for i in range(args.warmup + args.steps):
-        v, dt, cores, sample = cpu_oracle_sample(steps_per_pattern=1)
+        v, dt, cores, sample = cpu_oracle_sample(steps_per_pattern=1, repeats=1)
         if i >= args.warmup:
             vals.append((v, dt))
     value = statistics.median(v for v, _ in vals)
@@ -220,6 +274,9 @@ VARIANTS = {
                        "(split hi/lo operands, FP32-level accuracy), FP32 accumulate",
     "box9+star13-bf16": "Box-2D9P and Star-2D13P, 8192x8192, 1000 steps each, BF16 storage, FP32 arithmetic",
     "heat512": "Heat-2D 5-point (weights 0.2f), 512x512, 100 steps, FP32, zero boundary",
+    "slab": "Box-2D9P and Star-2D13P FP32 on one (8192 x N) x 8192 grid per pattern split in row slabs over "
+            "the N ranks (8192 rows each), ghost rows exchanged every S steps (NCCL point-to-point), "
+            "1000 steps, zero boundary",
     "scaling": "weak-scaling sweep of the paper's shape: Heat-5 (Star-2D5P), Box-9, Star-13 and Box-49 FP32 "
                "on square grids 128^2 .. 32768^2, 1000 steps each, plus Star-2D5P on 44800^2 (HBM "
                "roofline point); inputs tile the seeded 4096^2 field",
@@ -252,13 +309,25 @@ def _time_steps(step, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
-def run_variant(args, world, rank, local):
+_FIELDS = {}
+
+
+def _field(n: int, stream: int = 0):
+    """inputs.field(n, n, stream=stream), generated once per process."""
+    from paper_2605_07954_gb300 import inputs
+    key = (n, stream)
+    if key not in _FIELDS:
+        _FIELDS[key] = inputs.field(n, n, stream=stream)
+    return _FIELDS[key]
+
+
+def variant_line(args, name, world, local, steps, warmup, e2e=True):
+    """Time one variant workload; return its JSON line (without printing)."""
     import torch
     from paper_2605_07954_gb300 import Batch, inputs
     stream = torch.cuda.current_stream()
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
-    name = args.workload
-    line = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+    line = {"n_gpus": world, "steps": steps, "warmup": warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
     if name == "batched":
         sides, kinds = inputs.batch_spec(256)
@@ -268,82 +337,85 @@ def run_variant(args, world, rank, local):
             x = torch.from_numpy(f).cuda()
             grids.append(dict(x=x, out=torch.empty_like(x), weights=inputs.batch_grid_weights(kind, gi),
                               T=200))
-            host_in.append(torch.from_numpy(f).pin_memory())
+            host_in.append(torch.from_numpy(f).pin_memory() if e2e else None)
         b = Batch(grids, autotune=not args.no_autotune)
         info = b.info()
         units = float(info["point_steps"])
         sampler = ClockSampler(gpu_id)
         sampler.start()
-        ms = _time_steps(b.run, args.steps, args.warmup, stream)
+        ms = _time_steps(b.run, steps, warmup, stream)
         clocks = sampler.stop()
         b.status()
         ms = _max_over_ranks(world, ms)
-        # end to end: host inputs in, batch, host outputs out, every step
-        host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-
-        def e2e_step():
-            for g, h in zip(grids, host_in):
-                g["x"].copy_(h, non_blocking=True)
-            b.run()
-            for g, h in zip(grids, host_out):
-                h.copy_(g["out"], non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-        e2e_ms = _time_steps(e2e_step, max(1, min(args.steps, 3)), 1, stream)
-        nbytes = sum(h.numel() * 4 for h in host_in)
+        acc = {}
+        for g in range(256):
+            rec = stored_window(f"batch_grid{g}")
+            if rec is not None:
+                acc[f"grid{g}_{int(sides[g])}"] = check_output(grids[g]["out"], f"batch_grid{g}", 1e-5)
         line.update({
             "metric": "GStencil/s (FP32 batched: 256 grids, 200 steps)", "value": whole_job_rate(world, units, ms),
             "unit": "GStencil/s", "ms_per_step": ms, "dtype": "f32",
             "config": {"workload": VARIANTS[name], "grids": 256, "points": int(sum(int(s) ** 2 for s in sides)),
                        "T": 200, "batch": info, "l2": "inputs larger than L2 (152.6 M points, 610 MB per copy)"},
-            "gpu_launches": info["launches"] * args.steps,
-            "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
-                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                    "api": "stencil_run_batched with torch copies of pinned host grids"},
+            "gpu_launches": info["launches"] * steps,
+            "accuracy": acc,
             "clocks": clocks,
         })
+        if e2e:
+            host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+
+            def e2e_step():
+                for g, h in zip(grids, host_in):
+                    g["x"].copy_(h, non_blocking=True)
+                b.run()
+                for g, h in zip(grids, host_out):
+                    h.copy_(g["out"], non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+            e2e_ms = _time_steps(e2e_step, max(1, min(steps, 3)), 1, stream)
+            nbytes = sum(h.numel() * 4 for h in host_in)
+            line["e2e"] = {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
+                           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                           "api": "stencil_run_batched with torch copies of pinned host grids"}
         b.close()
     if name in _PLAN_VARIANTS:
         from paper_2605_07954_gb300 import Plan
         pats, n, T, dtype, compute = _PLAN_VARIANTS[name]
         tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
         esz = 4 if dtype == "f32" else 2
-        plans, xs, outs, hins, houts = {}, {}, {}, {}, {}
+        plans, xs, outs = {}, {}, {}
         for pn in pats:
-            f = inputs.field(n, n)
             kern = {"auto": "auto", "warp": "tc_warp", "umma": "tc_umma"}[args.tc_engine] \
                 if compute.startswith("tc") else "auto"
             plans[pn] = Plan(n, n, inputs.pattern_weights(pn), dtype=dtype, compute=compute, kernel=kern,
                              autotune=not args.no_autotune,
                              mma_n=args.mma_n if compute.startswith("tc") else 0)
-            hins[pn] = torch.from_numpy(f).to(tdt).pin_memory()
-            xs[pn] = hins[pn].cuda()
+            xs[pn] = torch.from_numpy(_field(n)).to(tdt).cuda()
             outs[pn] = torch.empty_like(xs[pn])
-            houts[pn] = torch.empty_like(hins[pn]).pin_memory()
 
         def step():
             for pn in pats:
                 plans[pn].run(xs[pn], T, out=outs[pn])
         sampler = ClockSampler(gpu_id)
         sampler.start()
-        ms = _time_steps(step, args.steps, args.warmup, stream)
+        ms = _time_steps(step, steps, warmup, stream)
         clocks = sampler.stop()
-        per = {pn: _time_steps(lambda pn=pn: plans[pn].run(xs[pn], T, out=outs[pn]), args.steps, 1, stream)
+        per = {pn: _time_steps(lambda pn=pn: plans[pn].run(xs[pn], T, out=outs[pn]), steps, 1, stream)
                for pn in pats}
         for pn in pats:
             plans[pn].status()
         ms = _max_over_ranks(world, ms)
-
-        def e2e_step():
-            for pn in pats:
-                xs[pn].copy_(hins[pn], non_blocking=True)
-                plans[pn].run(xs[pn], T, out=outs[pn])
-                houts[pn].copy_(outs[pn], non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-        e2e_ms = _time_steps(e2e_step, max(1, min(args.steps, 3)), 1, stream)
+        # FP32 gate for FP32 arithmetic on FP32 storage; BF16 storage 1e-2; the
+        # tensor-core engines are reported with a loose sanity bound only.
+        gate = 1e-5 * max(1.0, T / 1000.0)
+        if dtype != "f32":
+            gate = 1e-2
+        if compute in ("tc_tf32", "tc_bf16"):
+            gate = 5e-2
+        acc = {pn: check_output(outs[pn], f"{pn}_{n}_T{T}", gate) for pn in pats}
         units = float(len(pats)) * n * n * T
         peaks, _ = _peaks()
         info0 = plans[pats[0]].info()
-        k = info0["tb_depth"]
+        k = max(1, info0["tb_depth"])
         launch_ms = per[pats[0]] / plans[pats[0]].launches(T)
         alg_bytes = 2.0 * esz * n * n * k
         line.update({
@@ -355,7 +427,8 @@ def run_variant(args, world, rank, local):
                        "per_pattern_ms": per, "plans": {pn: plans[pn].info() for pn in pats},
                        "l2": "inputs larger than L2" if n * n * esz > 129e6 else
                              "grid fits in L2 (parity workload; not roofline-meaningful)"},
-            "gpu_launches": sum(plans[pn].launches(T) for pn in pats) * args.steps,
+            "gpu_launches": sum(plans[pn].launches(T) for pn in pats) * steps,
+            "accuracy": acc,
             "roofline_hbm_effective": {"achieved_gbs": alg_bytes / (launch_ms * 1e-3) / 1e9,
                                        "peak_gbs": peaks["hbm_gbs"],
                                        "frac": alg_bytes / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
@@ -365,11 +438,23 @@ def run_variant(args, world, rank, local):
                                            f"box49_umma_n{info0['mma_n']}_{dtype}_{n}" if info0["kernel"] == 5
                                            else f"box49_warp_{compute}_{n}")
                                        if compute.startswith("tc") else None},
-            "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
-                    "h2d_bytes_per_step": len(pats) * n * n * esz, "d2h_bytes_per_step": len(pats) * n * n * esz,
-                    "api": "Plan.run (stencil_run) with torch copies of pinned host grids"},
             "clocks": clocks,
         })
+        if e2e:
+            hins = {pn: torch.from_numpy(_field(n)).to(tdt).pin_memory() for pn in pats}
+            houts = {pn: torch.empty_like(hins[pn]).pin_memory() for pn in pats}
+
+            def e2e_step():
+                for pn in pats:
+                    xs[pn].copy_(hins[pn], non_blocking=True)
+                    plans[pn].run(xs[pn], T, out=outs[pn])
+                    houts[pn].copy_(outs[pn], non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+            e2e_ms = _time_steps(e2e_step, max(1, min(steps, 3)), 1, stream)
+            line["e2e"] = {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
+                           "h2d_bytes_per_step": len(pats) * n * n * esz,
+                           "d2h_bytes_per_step": len(pats) * n * n * esz,
+                           "api": "Plan.run (stencil_run) with torch copies of pinned host grids"}
         for pn in pats:
             plans[pn].close()
     if name == "scaling":
@@ -414,13 +499,48 @@ def run_variant(args, world, rank, local):
             "e2e": None,
             "clocks": clocks,
         })
+    if name == "slab":
+        # One (8192 * world) x 8192 grid per pattern, split in row slabs over the
+        # ranks, ghost rows exchanged (NCCL) before every block of S steps.
+        from paper_2605_07954_gb300.slab import SlabSweep
+        T, nx = 1000, 8192
+        ny = nx * world
+        S = {"box9": 8, "star13": 4}
+        sl = {}
+        for pn in PATTERNS:
+            s = SlabSweep(ny, nx, inputs.pattern_weights(pn), S[pn], "zero",
+                          rank=int(os.environ.get("RANK", "0")), world=world)
+            s.load(torch.from_numpy(_field(nx)).cuda())
+            sl[pn] = s
+
+        def step():
+            for pn in PATTERNS:
+                sl[pn].run(T)
+        sampler = ClockSampler(gpu_id)
+        sampler.start()
+        ms = _time_steps(step, steps, warmup, stream)
+        clocks = sampler.stop()
+        ms = _max_over_ranks(world, ms)
+        units = float(len(PATTERNS)) * nx * nx * T
+        line.update({
+            "metric": f"GStencil/s (row slabs: Box-2D9P + Star-2D13P, (8192 x {world}) x 8192, 1000 steps)",
+            "value": whole_job_rate(world, units, ms), "unit": "GStencil/s", "ms_per_step": ms,
+            "dtype": "f32",
+            "config": {"workload": VARIANTS[name], "ny": ny, "nx": nx, "T": T, "steps_per_exchange": S,
+                       "geometry": {pn: sl[pn].geom for pn in PATTERNS},
+                       "l2": "inputs larger than L2"},
+            "gpu_launches": None,
+            "e2e": None,
+            "clocks": clocks,
+        })
+        for pn in PATTERNS:
+            sl[pn].close()
     if name == "adjoint":
         from paper_2605_07954_gb300 import Plan, adjoint
         n, T = 4096, 512
         W = inputs.heat_weights(0.2)
-        h_u0 = torch.from_numpy(inputs.field(n, n)).pin_memory()
-        h_tg = torch.from_numpy(inputs.field(n, n, stream=inputs.STREAM_TARGET)).pin_memory()
-        u0, target = h_u0.cuda(), h_tg.cuda()
+        u0 = torch.from_numpy(_field(n)).cuda()
+        target = torch.from_numpy(_field(n, inputs.STREAM_TARGET)).cuda()
         plan = Plan(n, n, W, autotune=not args.no_autotune)
         holder = {}
 
@@ -436,23 +556,29 @@ def run_variant(args, world, rank, local):
             bwd()
         sampler = ClockSampler(gpu_id)
         sampler.start()
-        ms = _time_steps(step, args.steps, args.warmup, stream)
+        ms = _time_steps(step, steps, warmup, stream)
         clocks = sampler.stop()
-        fwd_ms = _time_steps(fwd, args.steps, 1, stream)
-        bwd_ms = _time_steps(bwd, args.steps, 1, stream)
+        fwd_ms = _time_steps(fwd, steps, 1, stream)
+        bwd_ms = _time_steps(bwd, steps, 1, stream)
         plan.status()
         ms = _max_over_ranks(world, ms)
-
-        def e2e_step():
-            u0.copy_(h_u0, non_blocking=True)
-            target.copy_(h_tg, non_blocking=True)
-            step()
-            gu, gw = holder["g"]
-            gu.cpu()
-            gw.cpu()
-        e2e_ms = _time_steps(e2e_step, max(1, min(args.steps, 3)), 1, stream)
         launches = plan.launches(T) + int(_capi_launches_adjoint(plan, T))
         units = float(n) * n * T
+        # accuracy: the same entry points on the 64 x 64 x 32 instance stored with its
+        # FP64 oracle gradients
+        rec = stored_window("adjoint_heat5_64_T32")
+        acc = {}
+        if rec is not None:
+            p64 = Plan(64, 64, W, kernel="stream")
+            a0 = torch.from_numpy(inputs.field(64, 64)).cuda()
+            tg = torch.from_numpy(inputs.field(64, 64, stream=inputs.STREAM_TARGET)).cuda()
+            gu, gw = adjoint(p64, a0, p64.run(a0, 32) - tg, 32)
+            torch.cuda.synchronize()
+            acc = {"grad_w": window_error(gw.cpu().numpy(), np.asarray(rec["grad_w"])),
+                   "grad_u0": window_error(gu[:16, :16].cpu().numpy(), np.asarray(rec["grad_u0_window"])),
+                   "instance": "Heat 64x64, 32 steps, vs FP64 oracle gradients", "gate_rel": 1e-4}
+            acc["ok"] = acc["grad_w"]["relL2"] <= 1e-4 and acc["grad_u0"]["relL2"] <= 1e-4
+            p64.close()
         line.update({
             "metric": "GStencil/s (Heat-2D FP32 forward + adjoint, 4096^2, 512 steps)",
             "value": whole_job_rate(world, units, ms), "unit": "GStencil/s", "ms_per_step": ms,
@@ -461,14 +587,32 @@ def run_variant(args, world, rank, local):
                        "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
                        "ckpt_interval": int(np.ceil(np.sqrt(T))), "plan": plan.info(),
                        "l2": "inputs larger than L2 (64 MiB per grid, 23 checkpoints)"},
-            "gpu_launches": launches * args.steps,
-            "e2e": {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
-                    "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4 + 9 * 8,
-                    "api": "Plan.run + stencil_adjoint (torch copies of pinned host u0/target, "
-                           "gradients read back)"},
+            "gpu_launches": launches * steps,
+            "accuracy": acc,
             "clocks": clocks,
         })
+        if e2e:
+            h_u0 = torch.from_numpy(_field(n)).pin_memory()
+            h_tg = torch.from_numpy(_field(n, inputs.STREAM_TARGET)).pin_memory()
+
+            def e2e_step():
+                u0.copy_(h_u0, non_blocking=True)
+                target.copy_(h_tg, non_blocking=True)
+                step()
+                gu, gw = holder["g"]
+                gu.cpu()
+                gw.cpu()
+            e2e_ms = _time_steps(e2e_step, max(1, min(steps, 3)), 1, stream)
+            line["e2e"] = {"value": whole_job_rate(world, units, e2e_ms), "unit": "GStencil/s",
+                           "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4 + 9 * 8,
+                           "api": "Plan.run + stencil_adjoint (torch copies of pinned host u0/target, "
+                                  "gradients read back)"}
         plan.close()
+    return line
+
+
+def run_variant(args, world, rank, local):
+    line = variant_line(args, args.workload, world, local, args.steps, args.warmup, e2e=True)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -505,6 +649,8 @@ def main():
     ap.add_argument("--profile-launch", action="store_true",
                     help="profiling captures: run each pattern's plan for exactly two launches of its "
                          "depth k (no timing, no JSON line), so ncu can capture the second one")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="headline workload: skip the short runs of the variant workloads")
     ap.add_argument("--tc-engine", default="auto", choices=["auto", "warp", "umma"],
                     help="tensor-core workloads: autotuned engine choice, warp-level MMAs, or tcgen05")
     ap.add_argument("--mma-n", type=int, default=0,
@@ -579,6 +725,9 @@ def main():
     for p in PATTERNS:
         plans[p].status()
     per_pattern_ms = {p: statistics.mean(e[p][0].elapsed_time(e[p][1]) for e in evs) for p in PATTERNS}
+    # The timed runs' own output against the stored FP64 oracle window (gate:
+    # relative L2 1e-5 per 1000 steps).
+    accuracy = {p: check_output(outs[p], f"{p}_{N}_T{T}", 1e-5 * max(1.0, T / 1000.0)) for p in PATTERNS}
 
     updates_per_step = len(PATTERNS) * N * N * T
     ms_per_step = ms_total / args.steps
@@ -627,6 +776,7 @@ def main():
                                        "hbm_frac_effective": 8.0 * N * N * T / (per_pattern_ms[p] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                        "plan": plans[p].info()} for p in PATTERNS}},
         "gpu_launches": launches_per_step * args.steps,
+        "accuracy": accuracy,
         "roofline": roofline,
         "clocks": clocks,
     }
@@ -650,19 +800,59 @@ def main():
                        "d2h_bytes_per_step": len(PATTERNS) * N * N * 4,
                        "steps": e2e_steps, "api": "stencil_run_host (pinned host buffers)"}
 
+    for p in PATTERNS:
+        plans[p].close()
+    if world == 1 and not args.no_variants:
+        line["variants"] = run_variant_samples(args, world, local)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores, sample = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": "GStencil/s", "cores": cores, "kind": "oracle",
-                                "sample": sample, "seconds": dt}
+                                "sample": sample, "seconds": dt,
+                                "heat512_single_thread": cpu_heat512_single_thread()}
 
-    for p in PATTERNS:
-        plans[p].close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# Variant workloads sampled on every default run (N = 1): each timed for 2
+# steps after 3 warm-up steps, its output checked against stored FP64 windows.
+DEFAULT_VARIANTS = ("box49", "box49-bf16", "box49-tc-tf32", "box49-tc-bf16", "box49-tc-3xtf32",
+                    "box9+star13-bf16", "batched", "adjoint", "heat512")
+
+
+def run_variant_samples(args, world, local) -> dict:
+    import torch
+    out = {}
+    for name in DEFAULT_VARIANTS:
+        t0 = time.perf_counter()
+        try:
+            v = variant_line(args, name, world, local, steps=2, warmup=3, e2e=False)
+        except Exception as e:  # a failing variant must not hide the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        finally:
+            torch.cuda.empty_cache()
+        cfg = v.get("config", {})
+        rec = {"metric": v["metric"], "value": v["value"], "unit": v["unit"], "ms_per_step": v["ms_per_step"],
+               "dtype": v["dtype"], "gpu_launches": v.get("gpu_launches"), "accuracy": v.get("accuracy"),
+               "wall_s": time.perf_counter() - t0}
+        if "roofline_hbm_effective" in v:
+            rec["hbm_effective_frac"] = v["roofline_hbm_effective"]["frac"]
+        if "plans" in cfg:
+            rec["plans"] = {pn: {k: i[k] for k in ("kernel", "tb_depth", "threads", "mma_n")}
+                            for pn, i in cfg["plans"].items()}
+        for key in ("forward_ms", "backward_ms", "backward_over_forward"):
+            if key in cfg:
+                rec[key] = cfg[key]
+        if "batch" in cfg:
+            rec["batch"] = {k: cfg["batch"][k] for k in ("tb_depth", "threads", "launches", "items")}
+        out[name] = rec
+    return out
 
 
 if __name__ == "__main__":

@@ -67,13 +67,22 @@ typedef enum { STENCIL_BOUNDARY_ZERO = 0, STENCIL_BOUNDARY_PERIODIC = 1 } stenci
  * accuracy: inputs and weights split into TF32 hi + lo parts and each
  * product is hi*hi + hi*lo + lo*hi (three MMAs, FP32-level error; warp-MMA
  * engine, FP32 storage only).  Storage FP32 or BF16.  Other radii or FP16
- * storage: STENCIL_ERR_UNSUPPORTED. */
+ * storage: STENCIL_ERR_UNSUPPORTED.
+ * LOWRANK (any radius, FP32 storage, either boundary): the weights are factored
+ * by an SVD into rho separable terms, W[dy][dx] = sum_k c_k[dy] v_k[dx] (rho =
+ * the numerical rank, singular values above 1e-6 of the largest, or
+ * options.rank), and each step runs as rho row passes and rho column passes
+ * in FP32 on the CUDA cores: 2 rho (2r+1) FMAs per point instead of (2r+1)^2,
+ * one step per launch.  Exact up to FP32 rounding of the factors when W has
+ * rank rho; a truncation otherwise (the paper's related work on low-rank
+ * tensor-core stencils, Sec. II-D). */
 typedef enum {
     STENCIL_COMPUTE_AUTO = 0,
     STENCIL_COMPUTE_FP32 = 1,
     STENCIL_COMPUTE_TC_TF32 = 2,
     STENCIL_COMPUTE_TC_BF16 = 3,
-    STENCIL_COMPUTE_TC_3XTF32 = 4
+    STENCIL_COMPUTE_TC_3XTF32 = 4,
+    STENCIL_COMPUTE_LOWRANK = 5
 } stencil_compute_t;
 
 /* Kernel family.  The tensor-core contraction (7x7 box, one step per launch)
@@ -92,8 +101,9 @@ typedef enum {
     STENCIL_KERNEL_TC = 3,         /* tensor cores: tcgen05 where it applies, else warp MMA */
     STENCIL_KERNEL_TC_WARP = 4,    /* tensor cores, warp-MMA engine only             */
     STENCIL_KERNEL_TC_UMMA = 5,    /* tensor cores, tcgen05 engine (UNSUPPORTED where it does not apply) */
-    STENCIL_KERNEL_RESIDENT = 6    /* small grids: the whole grid in one thread-block cluster's shared
+    STENCIL_KERNEL_RESIDENT = 6,   /* small grids: the whole grid in one thread-block cluster's shared
                                       memory, every step of a run in one launch                        */
+    STENCIL_KERNEL_LOWRANK = 7     /* chosen by compute = LOWRANK (reported by stencil_plan_info only) */
 } stencil_kernel_t;
 
 /* Optional plan settings; pass NULL for defaults.  0 means "choose".
@@ -116,11 +126,28 @@ typedef struct {
                          16, 32 (TF32): one weight row per MMA, 128 x 128 output
                          tiles; 96 or 128: three or four weight rows stacked in one
                          MMA over 32-column N-tiles, 126- or 125-row output tiles   */
-    int timeout_ms;   /* tcgen05 engine: limit of each device-side wait (0 = 2000)  */
+    int timeout_ms;   /* tcgen05 engine and TMA-fed streaming kernel: limit of each
+                         device-side wait in ms (0 = 2000)                             */
     int debug_withhold; /* test hook, 0 in normal use: 1 makes CTA 0 of the tcgen05
-                           engine withhold its first accumulator-ready signal, so its
-                           epilogue wait runs out and the run reports TIMEOUT         */
+                           engine withhold its first accumulator-ready signal, and CTA 0
+                           of the TMA-fed streaming kernel wait for 16 bytes more than
+                           its first row brings, so a wait runs out and the run
+                           reports TIMEOUT                                             */
+    int load;         /* streaming kernel's input rows: stencil_load_t                */
+    int rank;         /* compute = LOWRANK: separable terms kept (0 = numerical rank,
+                         else 1..2r+1)                                                 */
 } stencil_options_t;
+
+/* How the streaming kernel brings input rows into shared memory.  AUTO: the
+ * library default (and, with autotune, both timed).  CP_ASYNC: each thread
+ * copies its 16 bytes of every row (cp.async).  TMA: one thread issues 2D
+ * tensor copies of each row (cp.async.bulk.tensor, completion on an mbarrier;
+ * the copy engine's zero fill is the zero halo); FP32 storage, the zero rule
+ * and nx a multiple of 4 only (else STENCIL_ERR_UNSUPPORTED at create).  Each
+ * wait for a row is bounded by timeout_ms (an expired wait is reported as
+ * STENCIL_ERR_TIMEOUT by stencil_plan_status).  Same arithmetic and bits
+ * either way. */
+typedef enum { STENCIL_LOAD_AUTO = 0, STENCIL_LOAD_CP_ASYNC = 1, STENCIL_LOAD_TMA = 2 } stencil_load_t;
 
 /* What a plan decided.  Filled by stencil_plan_info(). */
 typedef struct {
@@ -137,6 +164,8 @@ typedef struct {
     int smem_bytes;        /* dynamic shared memory per CTA                         */
     int64_t workspace_bytes;  /* device workspace the plan owns                    */
     int mma_n;             /* tcgen05 engine in use: N of one MMA; 0 = not in use   */
+    int load;              /* streaming kernel's row loads (stencil_load_t); 0 = other kernel */
+    int rank;              /* LOWRANK: separable terms in use; 0 = other kernel      */
 } stencil_plan_info_t;
 
 typedef struct stencil_plan stencil_plan_t;
@@ -158,6 +187,15 @@ stencil_status_t stencil_plan_create(stencil_plan_t** plan, int64_t ny, int64_t 
 
 /* Release a plan and its device workspace.  NULL is accepted. */
 void stencil_plan_destroy(stencil_plan_t* plan);
+
+/* Replace the plan's weights (HOST, (2r+1)^2 FP32, copied) without creating a
+ * new plan: the workspace, the tuned configuration and any adjoint scratch are
+ * kept, so a training loop can update the weights every iteration.  Work
+ * already enqueued keeps the weights it was enqueued with.  The new weights
+ * must keep the footprint class (star or box) a streaming or cluster-resident
+ * plan was chosen for (else STENCIL_ERR_UNSUPPORTED, nothing changed); a
+ * LOWRANK plan refactors them. */
+stencil_status_t stencil_plan_set_weights(stencil_plan_t* plan, const float* weights);
 
 /* Report the plan's choices (after stencil_plan_create; tuning may refine them on first run). */
 stencil_status_t stencil_plan_info(const stencil_plan_t* plan, stencil_plan_info_t* info);

@@ -17,8 +17,10 @@ from ._capi import StencilError, check
 
 DTYPES = {"f32": _capi.STENCIL_F32, "bf16": _capi.STENCIL_BF16, "f16": _capi.STENCIL_F16}
 BOUNDARIES = {"zero": _capi.STENCIL_BOUNDARY_ZERO, "periodic": _capi.STENCIL_BOUNDARY_PERIODIC}
-COMPUTES = {"auto": 0, "fp32": 1, "tc_tf32": 2, "tc_bf16": 3, "tc_3xtf32": 4}
-KERNELS = {"auto": 0, "naive": 1, "stream": 2, "tc": 3, "tc_warp": 4, "tc_umma": 5, "resident": 6}
+COMPUTES = {"auto": 0, "fp32": 1, "tc_tf32": 2, "tc_bf16": 3, "tc_3xtf32": 4, "lowrank": 5}
+KERNELS = {"auto": 0, "naive": 1, "stream": 2, "tc": 3, "tc_warp": 4, "tc_umma": 5, "resident": 6,
+           "lowrank": 7}
+LOADS = {"auto": 0, "cp_async": 1, "tma": 2}
 
 
 def _torch_dtype_name(t) -> str:
@@ -37,7 +39,7 @@ class Plan:
     def __init__(self, ny: int, nx: int, weights, dtype: str = "f32", boundary: str = "zero",
                  compute: str = "auto", kernel: str = "auto", tb_depth: int = 0,
                  threads: int = 0, tile_rows: int = 0, autotune: bool = False, mma_n: int = 0,
-                 timeout_ms: int = 0, debug_withhold: int = 0):
+                 timeout_ms: int = 0, debug_withhold: int = 0, load: str = "auto", rank: int = 0):
         lib = _capi.load()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
         d = w.shape[0]
@@ -49,7 +51,7 @@ class Plan:
         self.weights = w
         opt = _capi.stencil_options_t(COMPUTES[compute], KERNELS[kernel], int(tb_depth),
                                       int(threads), int(tile_rows), int(bool(autotune)), int(mma_n),
-                                      int(timeout_ms), int(debug_withhold))
+                                      int(timeout_ms), int(debug_withhold), LOADS[load], int(rank))
         h = ctypes.c_void_p()
         check(lib.stencil_plan_create(ctypes.byref(h), int(ny), int(nx), self.radius,
                                       w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
@@ -71,6 +73,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_weights(self, weights) -> None:
+        """Replace the weights in place (stencil_plan_set_weights): same footprint class."""
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+        if w.shape != self.weights.shape:
+            raise ValueError(f"weights must be {self.weights.shape}, got {w.shape}")
+        check(_capi.load().stencil_plan_set_weights(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "stencil_plan_set_weights")
+        self.weights = w
 
     def info(self) -> dict:
         i = _capi.stencil_plan_info_t()
@@ -144,6 +155,35 @@ def adjoint(plan: Plan, u0, grad_uT, T: int, ckpt_interval: int = 0):
     return g_u0, g_w
 
 
+class _PlanCache:
+    """Plans for StencilFn, reused across calls: keyed by (device, shape,
+    radius, footprint class, boundary); a hit only replaces the weights
+    (stencil_plan_set_weights), so the workspace, the tuned configuration and
+    the adjoint's checkpoint scratch are allocated once, not per iteration.
+    At most `size` plans are kept (least recently used dropped first)."""
+
+    def __init__(self, size: int = 8):
+        self.size = size
+        self.plans = {}
+
+    def get(self, device: int, ny: int, nx: int, W: np.ndarray, boundary: str) -> Plan:
+        r = W.shape[0] // 2
+        star = bool(np.all(W[np.arange(W.shape[0]) != r][:, np.arange(W.shape[1]) != r] == 0))
+        key = (device, ny, nx, r, star, boundary)
+        plan = self.plans.pop(key, None)
+        if plan is None:
+            plan = Plan(ny, nx, W, boundary=boundary)
+            while len(self.plans) >= self.size:
+                self.plans.pop(next(iter(self.plans))).close()
+        else:
+            plan.set_weights(W)
+        self.plans[key] = plan  # most recently used last
+        return plan
+
+
+_PLANS = _PlanCache()
+
+
 def _stencil_fn():
     import torch
 
@@ -153,22 +193,27 @@ def _stencil_fn():
         apply(u0, weights, T, boundary="zero", ckpt_interval=0): u0 a CUDA FP32
         tensor; weights a (2r+1, 2r+1) tensor on any device (its values are read
         at forward time).  The weight gradient has the weights' dtype and device.
+        Plans come from a small per-process cache (see _PlanCache), so repeated
+        calls with new weights allocate nothing new.  The backward pass uses the
+        weights of its own forward call, read back from the saved copy.
         """
 
         @staticmethod
         def forward(ctx, u0, weights, T, boundary="zero", ckpt_interval=0):
-            W = weights.detach().to("cpu", torch.float32).numpy()
-            plan = Plan(u0.shape[0], u0.shape[1], W, boundary=boundary)
+            W = np.ascontiguousarray(weights.detach().to("cpu", torch.float32).numpy())
+            plan = _PLANS.get(u0.device.index if u0.is_cuda else -1, u0.shape[0], u0.shape[1], W, boundary)
             u0c = u0.detach().contiguous()
             y = plan.run(u0c, int(T))
             ctx.save_for_backward(u0c)
-            ctx.plan, ctx.T, ctx.ckpt = plan, int(T), int(ckpt_interval)
+            ctx.plan, ctx.W, ctx.T, ctx.ckpt = plan, W, int(T), int(ckpt_interval)
             ctx.wdtype, ctx.wdevice = weights.dtype, weights.device
             return y
 
         @staticmethod
         def backward(ctx, grad_y):
             (u0,) = ctx.saved_tensors
+            # another forward call may have changed the cached plan's weights
+            ctx.plan.set_weights(ctx.W)
             g_u0, g_w = adjoint(ctx.plan, u0, grad_y.contiguous(), ctx.T, ctx.ckpt)
             return g_u0, g_w.to(ctx.wdevice, ctx.wdtype), None, None, None
 

@@ -29,7 +29,8 @@ STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_STREAM = 0, 1, 2
 class stencil_options_t(ctypes.Structure):
     _fields_ = [("compute", ctypes.c_int), ("kernel", ctypes.c_int), ("tb_depth", ctypes.c_int),
                 ("threads", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("mma_n", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("debug_withhold", ctypes.c_int)]
+                ("mma_n", ctypes.c_int), ("timeout_ms", ctypes.c_int), ("debug_withhold", ctypes.c_int),
+                ("load", ctypes.c_int), ("rank", ctypes.c_int)]
 
 
 class stencil_plan_info_t(ctypes.Structure):
@@ -38,7 +39,8 @@ class stencil_plan_info_t(ctypes.Structure):
                 ("compute", ctypes.c_int), ("kernel", ctypes.c_int), ("tb_depth", ctypes.c_int),
                 ("threads", ctypes.c_int), ("halo_cols", ctypes.c_int), ("tile_cols", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("ctas", ctypes.c_int), ("smem_bytes", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_int64), ("mma_n", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_int64), ("mma_n", ctypes.c_int), ("load", ctypes.c_int),
+                ("rank", ctypes.c_int)]
 
 
 class stencil_grid_desc_t(ctypes.Structure):
@@ -78,6 +80,7 @@ _PROTOS = {
                                    ctypes.POINTER(stencil_options_t)]),
     "stencil_plan_destroy": (None, [_vp]),
     "stencil_plan_info": (_i32, [_vp, ctypes.POINTER(stencil_plan_info_t)]),
+    "stencil_plan_set_weights": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "stencil_run": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "stencil_run_host": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "stencil_run_launches": (_i64, [_vp, _i64]),

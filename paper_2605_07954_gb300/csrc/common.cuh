@@ -39,6 +39,9 @@ struct StreamParams {
     int strips;    // strips along x; blockIdx.x = strip + strips * row_tile
     int periodic;  // 1: wrap indices; 0: zero outside the grid
     int vec;       // 1: rows 16-byte aligned for 4-element vector access
+    unsigned* status;   // TMA-fed kernels: device status word (bounded waits), else unused
+    long long wait_ns;  // TMA-fed kernels: limit of each wait for a row
+    int debug_withhold; // TMA-fed kernels, test hook: CTA 0 expects 16 bytes its first row never brings
     Weights w;
     WeightPairs w2;
 };

@@ -30,7 +30,14 @@ GBST_DECL_STREAM(1, f32) GBST_DECL_STREAM(1, bf16) GBST_DECL_STREAM(1, f16)
 GBST_DECL_STREAM(2, f32) GBST_DECL_STREAM(2, bf16) GBST_DECL_STREAM(2, f16)
 GBST_DECL_STREAM(3, f32) GBST_DECL_STREAM(3, bf16) GBST_DECL_STREAM(3, f16)
 #undef GBST_DECL_STREAM
+StreamKernelRef get_stream_tma_kernel_r1(int star, int k);
+StreamKernelRef get_stream_tma_kernel_r2(int star, int k);
+StreamKernelRef get_stream_tma_kernel_r3(int star, int k);
 const void* get_naive_kernel(int radius, int dtype);
+int lowrank_factor(const float* w, int R, int rank, float col[7][7], float row[7][7], double* sv);
+const void* get_lowrank_kernel(int R, int rho);
+cudaError_t launch_lowrank(const void* fn, const float* src, float* dst, long long ny, long long nx, int periodic,
+                           const float col[7][7], const float row[7][7], int sms, cudaStream_t st);
 const void* get_box49_tc_kernel(int dtype, int engine);       // engine: 0 TF32, 1 BF16, 2 3xTF32
 const void* get_box49_tc_pipe_kernel(int dtype, int engine);
 int box49_tc_smem_bytes(int engine);
@@ -89,6 +96,11 @@ struct stencil_plan {
     int kernel = STENCIL_KERNEL_STREAM;
     int k = 1, threads = 0, H = 0, bx = 0, by = 0, strips = 0, tiles_y = 0, smem = 0;
     int per_sm = 0;
+    int tma = 0;  // streaming kernel fed by the tensor-memory-access engine
+    // separable (low-rank) form of the weights: rank and FP32 factors
+    int lr_rank = 0;
+    float lr_col[7][7] = {}, lr_row[7][7] = {};
+    const void* lr_fn = nullptr;
     const void* tc_pipe = nullptr;  // persistent double-buffered tensor-core kernel
     int tc_pipe_smem = 0, tc_pipe_ctas = 0;
     int umma_n = 0;     // tcgen05 engine in use: N of one MMA (0: warp-MMA engine)
@@ -160,20 +172,76 @@ static int default_depth(int R, int star) {
 }
 
 static const int kDefaultThreads = 128;
+// Row loads before tuning where both apply: 1 = the TMA-fed ring.
+static const int kDefaultTma = 0;
 
-// The depth-`depth` streaming kernel (VEC or element-wise variant), with its
-// shared-memory attribute set on first use.
-static stencil_status_t stream_fn(stencil_plan* p, int depth, int vec, const void** fn, int* smem) {
-    StreamKernelRef r = stream_kernel(p->R, p->star, depth, p->dtype, vec);
+// Plans whose rows the TMA-fed streaming kernel can load: FP32 storage, the
+// zero rule (the copy engine's zero fill is the zero halo) and rows of a
+// multiple of 16 bytes (the tensor map's row pitch).
+static bool tma_eligible(const stencil_plan* p) {
+    return p->dtype == STENCIL_F32 && p->boundary == STENCIL_BOUNDARY_ZERO && p->nx % 4 == 0;
+}
+
+static StreamKernelRef stream_tma_kernel(int R, int star, int k) {
+    switch (R) {
+        case 1: return get_stream_tma_kernel_r1(star, k);
+        case 2: return get_stream_tma_kernel_r2(star, k);
+        case 3: return get_stream_tma_kernel_r3(star, k);
+        default: return {nullptr, 0};
+    }
+}
+
+// The depth-`depth` streaming kernel (TMA-fed, VEC or element-wise variant),
+// with its shared-memory attribute set on first use.
+static stencil_status_t stream_fn(stencil_plan* p, int depth, int vec, const void** fn, int* smem,
+                                  int tma = -1) {
+    if (tma < 0) tma = p->tma;
+    tma = tma && vec;
+    StreamKernelRef r = tma ? stream_tma_kernel(p->R, p->star, depth)
+                            : stream_kernel(p->R, p->star, depth, p->dtype, vec);
     if (!r.fn) return fail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for depth " + std::to_string(depth));
-    *smem = stream_smem_bytes(p->R, depth, (int)p->elem, vec != 0);
-    const unsigned bit = 1u << (2 * depth + (vec ? 1 : 0));
+    *smem = stream_smem_bytes(p->R, depth, (int)p->elem, vec != 0, tma != 0);
+    const unsigned bit = 1u << (2 * depth + (vec ? 1 : 0) + (tma ? 16 : 0));
     if (!(p->smem_set & bit)) {
         CK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
         p->smem_set |= bit;
     }
     *fn = r.fn;
     return STENCIL_OK;
+}
+
+// Tensor map of an FP32 grid for the TMA-fed streaming kernel: nx x ny
+// elements, row pitch ld, boxes of kStreamTmaBox columns x 1 row, zero fill.
+typedef CUresult (*TmaEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static TmaEncodeFn tma_encoder() {
+    static TmaEncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && ptr)
+            fn = reinterpret_cast<TmaEncodeFn>(ptr);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+static bool stream_tensor_map(CUtensorMap* map, const void* src, int64_t ny, int64_t nx) {
+    TmaEncodeFn enc = tma_encoder();
+    if (!enc || (uintptr_t)src % 16 != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kStreamTmaBox, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(src), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Fill the streaming kernel's tile configuration for depth k and CTA size threads.
@@ -390,6 +458,27 @@ static stencil_status_t configure_naive(stencil_plan* p) {
     return STENCIL_OK;
 }
 
+// Separable form (compute = LOWRANK): factor the weights, one step per launch.
+static stencil_status_t configure_lowrank(stencil_plan* p) {
+    if (p->dtype != STENCIL_F32) return fail(STENCIL_ERR_UNSUPPORTED, "the low-rank form takes FP32 storage");
+    if (p->opt.kernel != STENCIL_KERNEL_AUTO)
+        return fail(STENCIL_ERR_UNSUPPORTED, "the low-rank form has its own kernel (kernel must be AUTO)");
+    p->lr_rank = lowrank_factor(p->w.w, p->R, p->opt.rank, p->lr_col, p->lr_row, nullptr);
+    if (p->lr_rank < 1) p->lr_rank = 1;  // all-zero weights: one zero term
+    p->lr_fn = get_lowrank_kernel(p->R, p->lr_rank);
+    if (!p->lr_fn) return fail(STENCIL_ERR_UNSUPPORTED, "no low-rank kernel for this rank");
+    p->kernel = STENCIL_KERNEL_LOWRANK;
+    p->k = 1;
+    p->threads = 128;
+    p->H = p->R;
+    p->bx = 128;
+    p->strips = (int)ceil_div(p->nx, 128);
+    p->tiles_y = 1;
+    p->by = (int)p->ny;
+    p->smem = 0;
+    return STENCIL_OK;
+}
+
 // One launch advancing `nlev` steps from src to dst.  `first` / `last`: this
 // launch starts / ends a run (the pipelined TF32 engine rounds its input on
 // the first launch and keeps intermediate states TF32-rounded until the last).
@@ -445,6 +534,11 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
         CK(launch_resident(p->res_fn, p->res_c, p->res_smem, rp, st));
         return STENCIL_OK;
     }
+    if (p->kernel == STENCIL_KERNEL_LOWRANK) {
+        CK(launch_lowrank(p->lr_fn, static_cast<const float*>(src), static_cast<float*>(dst), p->ny, p->nx,
+                          p->boundary == STENCIL_BOUNDARY_PERIODIC, p->lr_col, p->lr_row, p->sms, st));
+        return STENCIL_OK;
+    }
     if (p->kernel == STENCIL_KERNEL_NAIVE) {
         dim3 block(32, 8), grid((unsigned)p->strips, (unsigned)p->tiles_y);
         long long ny = p->ny, nx = p->nx;
@@ -470,13 +564,25 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
              ((uintptr_t)dst % vec_bytes == 0);
     sp.w = p->w;
     for (int i = 0; i < kMaxTaps; ++i) sp.w2.w2[i] = make_float2(p->w.w[i], p->w.w[i]);
+    sp.status = p->status;
+    sp.wait_ns = (long long)(p->opt.timeout_ms > 0 ? p->opt.timeout_ms : 2000) * 1000000LL;
+    sp.debug_withhold = p->opt.debug_withhold;
+    dim3 grid((unsigned)(p->strips * p->tiles_y)), block((unsigned)p->threads);
     const void* fn = nullptr;
     int smem = 0;
-    stencil_status_t s = stream_fn(p, nlev, sp.vec, &fn, &smem);
+    alignas(64) CUtensorMap map;
+    // The TMA-fed kernel when the plan uses it and this source has a tensor
+    // map (16-byte aligned); otherwise the cp.async kernel, same arithmetic.
+    const int tma = p->tma && sp.vec && stream_tensor_map(&map, src, p->ny, p->nx);
+    stencil_status_t s = stream_fn(p, nlev, sp.vec, &fn, &smem, tma);
     if (s != STENCIL_OK) return s;
-    void* args[] = {&sp};
-    dim3 grid((unsigned)(p->strips * p->tiles_y)), block((unsigned)p->threads);
-    CK(cudaLaunchKernel(fn, grid, block, args, (size_t)smem, st));
+    if (tma) {
+        void* args[] = {&map, &sp};
+        CK(cudaLaunchKernel(fn, grid, block, args, (size_t)smem, st));
+    } else {
+        void* args[] = {&sp};
+        CK(cudaLaunchKernel(fn, grid, block, args, (size_t)smem, st));
+    }
     return STENCIL_OK;
 }
 
@@ -588,36 +694,47 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end())
-            return configure_stream(p, it->second.first, it->second.second, p->opt.tile_rows);
+        if (it != g_tune_cache.end()) {
+            p->tma = it->second.second >> 16;
+            return configure_stream(p, it->second.first, it->second.second & 0xffff, p->opt.tile_rows);
+        }
     }
     const int ths[3] = {64, 128, 256};
     float best = 1e30f;
-    int bk = p->k, bt = p->threads;
+    int bk = p->k, bt = p->threads, btma = p->tma;
     const double points = (double)p->ny * (double)p->nx;
-    for (int i = 0; i < 8 && kStreamDepths[p->R - 1][p->star][i]; ++i) {
-        const int k = kStreamDepths[p->R - 1][p->star][i];
-        if (p->opt.tb_depth > 0 && k != p->opt.tb_depth) continue;
-        for (int th : ths) {
-            if (p->opt.threads > 0 && th != p->opt.threads) continue;
-            if (configure_stream(p, k, th, p->opt.tile_rows) != STENCIL_OK) continue;
-            // About 2e9 point-steps of work per candidate, at least one launch.
-            const int reps = (int)std::max(1.0, std::min(64.0, 2e9 / (points * k)));
-            float ms = 0.f;
-            stencil_status_t s = time_launch(p, in, reps, st, &ms);
-            if (s != STENCIL_OK) return s;
-            const float per_step = ms / (float)(reps * k);
-            if (per_step < best) {
-                best = per_step;
-                bk = k;
-                bt = th;
+    // Row loads: both the cp.async ring and the TMA-fed ring where the plan
+    // allows either (load = AUTO), else the one it fixed.
+    const int tma_lo = p->opt.load == STENCIL_LOAD_TMA ? 1 : 0;
+    const int tma_hi = (p->opt.load != STENCIL_LOAD_CP_ASYNC && tma_eligible(p)) ? 1 : 0;
+    for (int tma = tma_lo; tma <= tma_hi; ++tma) {
+        p->tma = tma;
+        for (int i = 0; i < 8 && kStreamDepths[p->R - 1][p->star][i]; ++i) {
+            const int k = kStreamDepths[p->R - 1][p->star][i];
+            if (p->opt.tb_depth > 0 && k != p->opt.tb_depth) continue;
+            for (int th : ths) {
+                if (p->opt.threads > 0 && th != p->opt.threads) continue;
+                if (configure_stream(p, k, th, p->opt.tile_rows) != STENCIL_OK) continue;
+                // About 2e9 point-steps of work per candidate, at least one launch.
+                const int reps = (int)std::max(1.0, std::min(64.0, 2e9 / (points * k)));
+                float ms = 0.f;
+                stencil_status_t s = time_launch(p, in, reps, st, &ms);
+                if (s != STENCIL_OK) return s;
+                const float per_step = ms / (float)(reps * k);
+                if (per_step < best) {
+                    best = per_step;
+                    bk = k;
+                    bt = th;
+                    btma = tma;
+                }
             }
         }
     }
+    p->tma = btma;
     stencil_status_t s = configure_stream(p, bk, bt, p->opt.tile_rows);
     if (s != STENCIL_OK) return s;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_cache[key] = std::make_pair(bk, bt);
+    g_tune_cache[key] = std::make_pair(bk, bt | (btma << 16));
     return STENCIL_OK;
 }
 
@@ -721,9 +838,10 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
         return fail(STENCIL_ERR_INVALID_ARG, "bad boundary");
     stencil_options_t o{};
     if (opt) o = *opt;
-    if (o.compute < 0 || o.compute > STENCIL_COMPUTE_TC_3XTF32 || o.kernel < 0 ||
+    if (o.compute < 0 || o.compute > STENCIL_COMPUTE_LOWRANK || o.kernel < 0 ||
         o.kernel > STENCIL_KERNEL_RESIDENT || o.tb_depth < 0 || o.threads < 0 || o.tile_rows < 0 ||
-        o.mma_n < 0 || o.timeout_ms < 0 || o.debug_withhold < 0 || o.debug_withhold > 1)
+        o.mma_n < 0 || o.timeout_ms < 0 || o.debug_withhold < 0 || o.debug_withhold > 1 ||
+        o.load < STENCIL_LOAD_AUTO || o.load > STENCIL_LOAD_TMA || o.rank < 0 || o.rank > 2 * radius + 1)
         return fail(STENCIL_ERR_INVALID_ARG, "bad option value");
 
     stencil_plan* p = new (std::nothrow) stencil_plan();
@@ -734,7 +852,7 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     p->dtype = dtype;
     p->boundary = boundary;
     p->compute = (o.compute == STENCIL_COMPUTE_TC_TF32 || o.compute == STENCIL_COMPUTE_TC_BF16 ||
-                  o.compute == STENCIL_COMPUTE_TC_3XTF32)
+                  o.compute == STENCIL_COMPUTE_TC_3XTF32 || o.compute == STENCIL_COMPUTE_LOWRANK)
                      ? o.compute : STENCIL_COMPUTE_FP32;
     p->opt = o;
     p->elem = elem_size(dtype);
@@ -770,7 +888,9 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     stencil_status_t st;
     const bool tc_kernel = o.kernel == STENCIL_KERNEL_TC || o.kernel == STENCIL_KERNEL_TC_WARP ||
                            o.kernel == STENCIL_KERNEL_TC_UMMA;
-    if (p->compute != STENCIL_COMPUTE_FP32 || tc_kernel) {
+    if (p->compute == STENCIL_COMPUTE_LOWRANK) {
+        st = configure_lowrank(p);
+    } else if (p->compute != STENCIL_COMPUTE_FP32 || tc_kernel) {
         if (p->compute == STENCIL_COMPUTE_FP32) p->compute = STENCIL_COMPUTE_TC_TF32;
         st = configure_tc(p);
     } else if (o.kernel == STENCIL_KERNEL_NAIVE) {
@@ -778,6 +898,10 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
     } else {
         const int k = o.tb_depth > 0 ? o.tb_depth : default_depth(radius, star);
         const int threads = o.threads > 0 ? o.threads : kDefaultThreads;
+        if (o.load == STENCIL_LOAD_TMA && !tma_eligible(p))
+            return bail(fail(STENCIL_ERR_UNSUPPORTED,
+                             "TMA-fed rows need FP32 storage, the zero rule and nx a multiple of 4"));
+        p->tma = o.load == STENCIL_LOAD_TMA || (o.load == STENCIL_LOAD_AUTO && tma_eligible(p) && kDefaultTma);
         st = configure_stream(p, std::min(k, stream_kmax(radius, star)), threads, o.tile_rows);
         // Small grids: the cluster-resident kernel, unless the caller asked for
         // the streaming kernel or set one of its options.
@@ -825,6 +949,36 @@ void stencil_plan_destroy(stencil_plan_t* p) {
     delete p;
 }
 
+stencil_status_t stencil_plan_set_weights(stencil_plan_t* p, const float* weights) {
+    if (!p || !weights) return fail(STENCIL_ERR_INVALID_ARG, "NULL argument");
+    const int R = p->R, D = 2 * R + 1;
+    int star = 1;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            const float v = weights[a * D + b];
+            if (!std::isfinite(v)) return fail(STENCIL_ERR_INVALID_ARG, "weights must be finite");
+            if (a != R && b != R && v != 0.f) star = 0;
+        }
+    const bool footprint_bound = p->kernel == STENCIL_KERNEL_STREAM || p->kernel == STENCIL_KERNEL_RESIDENT;
+    if (footprint_bound && star != p->star)
+        return fail(STENCIL_ERR_UNSUPPORTED,
+                    "the new weights change the footprint (star / box) the plan's kernel was chosen for");
+    if (p->kernel == STENCIL_KERNEL_LOWRANK) {
+        float col[7][7], row[7][7];
+        int rho = lowrank_factor(weights, R, p->opt.rank, col, row, nullptr);
+        if (rho < 1) rho = 1;
+        const void* fn = get_lowrank_kernel(R, rho);
+        if (!fn) return fail(STENCIL_ERR_UNSUPPORTED, "no low-rank kernel for this rank");
+        p->lr_rank = rho;
+        p->lr_fn = fn;
+        std::memcpy(p->lr_col, col, sizeof(col));
+        std::memcpy(p->lr_row, row, sizeof(row));
+    }
+    for (int i = 0; i < D * D; ++i) p->w.w[i] = weights[i];
+    if (!footprint_bound) p->star = star;
+    return STENCIL_OK;
+}
+
 stencil_status_t stencil_plan_info(const stencil_plan_t* p, stencil_plan_info_t* info) {
     if (!p || !info) return fail(STENCIL_ERR_INVALID_ARG, "NULL argument");
     stencil_plan_info_t i{};
@@ -845,6 +999,8 @@ stencil_status_t stencil_plan_info(const stencil_plan_t* p, stencil_plan_info_t*
     i.smem_bytes = p->smem;
     i.workspace_bytes = (int64_t)((size_t)p->ny * p->nx * p->elem);
     i.mma_n = p->umma_n;
+    i.load = p->kernel == STENCIL_KERNEL_STREAM ? (p->tma ? STENCIL_LOAD_TMA : STENCIL_LOAD_CP_ASYNC) : 0;
+    i.rank = p->kernel == STENCIL_KERNEL_LOWRANK ? p->lr_rank : 0;
     if (p->kernel == STENCIL_KERNEL_RESIDENT) {
         i.tb_depth = 0;  // every step of a run in one launch
         i.threads = resident_threads();

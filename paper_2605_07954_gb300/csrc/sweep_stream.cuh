@@ -50,8 +50,11 @@
 // (zero) weights.  The order depends neither on K nor on the tile shape.
 #pragma once
 
+#include <cuda.h>
+
 #include <type_traits>
 
+#include "../../include/stencil.h"
 #include "common.cuh"
 
 namespace gbst {
@@ -65,9 +68,15 @@ __host__ __device__ constexpr int stream_buf_floats(int R) {
     return R == 3 ? 4 * (kStreamMaxThreads + 2) : 2 * R * (kStreamMaxThreads + 2);
 }
 
-// Dynamic shared memory of a launch: the input ring (VEC only) + 2K edge buffers.
-__host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes, bool vec) {
-    return (vec ? kStreamPrefetch * kStreamMaxThreads * 4 * elem_bytes : 0) +
+// TMA-fed kernels: the ring's row mbarriers and the abort flag, after the ring.
+constexpr int kStreamTmaCtlBytes = 128;
+// Columns of one TMA box (one 512-byte piece of an FP32 ring row).
+constexpr int kStreamTmaBox = 128;
+
+// Dynamic shared memory of a launch: the input ring (VEC only), the TMA
+// control block (TMA-fed kernels) and 2K edge buffers.
+__host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes, bool vec, bool tma = false) {
+    return (vec ? kStreamPrefetch * kStreamMaxThreads * 4 * elem_bytes : 0) + (tma ? kStreamTmaCtlBytes : 0) +
            2 * K * stream_buf_floats(R) * 4;
 }
 
@@ -113,6 +122,78 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, bool 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// ---- TMA-fed ring (FP32 storage, zero rule, rows 16-byte aligned) -------------------
+//
+// One thread loads each input row of the strip with 2D tensor copies of
+// kStreamTmaBox columns x 1 row into the ring slot; out-of-grid columns and
+// rows are filled with zeros by the copy engine, which is the zero rule.
+// Each slot has an mbarrier that the copies complete; every thread waits on
+// it, with a time limit (an expired wait records STENCIL_ERR_TIMEOUT, raises
+// the CTA's abort flag and the tile finishes without waiting again).
+
+struct TmaRing {
+    const CUtensorMap* map = nullptr;
+    unsigned bar0 = 0;             // shared address of slot 0's mbarrier
+    volatile int* abort = nullptr;  // CTA-wide flag in shared memory
+};
+
+__device__ __forceinline__ unsigned st_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void st_bar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void st_bar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool st_bar_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ long long st_now() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void st_tma_row(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Wait for phase `parity` of `bar`; false if the CTA aborted or the limit ran out.
+static __device__ __noinline__ bool st_wait_slow(unsigned bar, unsigned parity, volatile int* abort, unsigned* status,
+                                          long long limit_ns) {
+    const long long t0 = st_now();
+    for (unsigned it = 0;; ++it) {
+        if (st_bar_try(bar, parity)) return true;
+        if (*abort) return false;
+        if ((it & 63u) == 63u && (st_now() - t0 > limit_ns || it > (1u << 26))) {
+            atomicCAS(status, 0u, (unsigned)STENCIL_ERR_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void st_wait(unsigned bar, unsigned parity, volatile int* abort, unsigned* status,
+                                        long long limit_ns) {
+    if (st_bar_try(bar, parity) || *abort) return;
+    st_wait_slow(bar, parity, abort, status, limit_ns);
+}
 
 template <typename TS>
 __device__ __forceinline__ void smem_chunk_to_f32(const void* src, float (&v)[4]) {
@@ -368,9 +449,10 @@ __host__ __device__ constexpr int stream_rows_after(int R, int K) {
 // row (zero rule, edge tiles) and, at the top level, stores it.  Per output the
 // products are still added row by row (dy = -R .. R), own columns before
 // neighbour columns, so the result does not depend on the schedule or on K.
-template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, class WS>
+template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, bool TMA = false, class WS>
 __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws, char* ring,
-                                            float* ebuf, int NT, int tid, int x0, int y0) {
+                                            float* ebuf, int NT, int tid, int x0, int y0,
+                                            TmaRing tma = TmaRing{}) {
     constexpr int D = 2 * R + 1;
     constexpr int SZ = stream_buf_floats(R);
     constexpr int PF = kStreamPrefetch;
@@ -410,6 +492,37 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
     char* my_ring = ring + tid * CB;
     const TS* my_src = gin + (EDGE ? 0 : (ptrdiff_t)ybeg * (ptrdiff_t)ld + c0);
     auto issue_row = [&](int s) {
+        if constexpr (TMA) {
+            // Warp 0 copies the strip's row ybeg + s into ring slot s % PF: lane b
+            // issues box b (kStreamTmaBox columns), lane 0 also arms the slot's
+            // mbarrier with the row's byte count.  The slot last held row s - PF,
+            // read by every thread at that row step, before a barrier this warp
+            // has passed since; each issuing lane's proxy fence orders those reads
+            // before the copy engine's writes.
+            const int nbox = (NT * 4) / kStreamTmaBox;
+            if (tid < nbox && s < nsteps && !*tma.abort) {
+                const int slot = s & (PF - 1);
+                const unsigned bar = tma.bar0 + 8u * (unsigned)slot;
+                const unsigned dst = st_smem(ring + slot * (kStreamMaxThreads * CB)) + (unsigned)(tid * kStreamTmaBox * 4);
+                const int xs = x0 - p.H + tid * kStreamTmaBox;
+                // the copy's first column must be 16-byte aligned, and so must its
+                // destination (128 bytes: every box starts on a 512-byte boundary)
+                if ((xs & 3) || (dst & 127u)) {
+                    atomicCAS(p.status, 0u, (unsigned)STENCIL_ERR_DEVICE_CHECK);
+                    *tma.abort = 1;
+                    return;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (tid == 0) {
+                    // (test hook: CTA 0 waits for 16 bytes more than its first row
+                    // brings, so that wait runs out and the timeout path is exercised)
+                    const unsigned extra = (p.debug_withhold && blockIdx.x == 0 && s == 0) ? 16u : 0u;
+                    st_bar_expect_tx(bar, (unsigned)(nbox * kStreamTmaBox * 4) + extra);
+                }
+                st_tma_row(dst, tma.map, xs, ybeg + s, bar);
+            }
+            return;
+        }
         bool ok = s < nsteps;
         const TS* src;
         if constexpr (EDGE) {
@@ -430,7 +543,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
     };
 
     float nreg0[4], nreg1[4];  // register prefetch (non-VEC)
-    if constexpr (VEC) {
+    if constexpr (VEC || TMA) {
 #pragma unroll
         for (int s = 0; s < PF - 1; ++s) issue_row(s);
     } else {
@@ -445,7 +558,12 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
             const int cin = (j + R) % D;        // slot completed at the previous step
             const int cdone = (j + R + 1) % D;  // slot completed at this step
             float cur[4];                       // level 0's input row
-            if constexpr (VEC) {
+            if constexpr (TMA) {
+                issue_row(s + PF - 1);
+                st_wait(tma.bar0 + 8u * (unsigned)(s & (PF - 1)), (unsigned)((s / PF) & 1), tma.abort, p.status,
+                        p.wait_ns);
+                smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), cur);
+            } else if constexpr (VEC) {
                 issue_row(s + PF - 1);
                 cp_async_wait<PF - 1>();
                 smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), cur);
@@ -606,7 +724,11 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
             }  // hand-over
         }
     }
-    if constexpr (VEC) cp_async_wait<0>();
+    if constexpr (TMA) {
+        __syncthreads();  // every thread is done with the ring before the next tile's rows arrive
+    } else if constexpr (VEC) {
+        cp_async_wait<0>();
+    }
 }
 
 template <int R, bool STAR, int K, typename TS, bool VEC>
@@ -638,6 +760,47 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
         stream_tile<R, STAR, K, TS, VEC, false>(p, ws, ring, ebuf, NT, tid, x0, y0);
     else
         stream_tile<R, STAR, K, TS, VEC, true>(p, ws, ring, ebuf, NT, tid, x0, y0);
+}
+
+// The same sweep with the input rows brought in by the tensor-memory-access
+// engine (FP32 storage, zero rule, rows of a multiple of 4 elements): `map`
+// describes the input grid (nx x ny, row pitch ld, box kStreamTmaBox x 1).
+template <int R, bool STAR, int K>
+__global__ void __launch_bounds__(kStreamMaxThreads)
+    sweep_stream_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ StreamParams p) {
+    constexpr int PF = kStreamPrefetch;
+    constexpr int CB = 16;
+    extern __shared__ __align__(1024) float4 smem_tma[];
+    char* ring = reinterpret_cast<char*>(smem_tma);
+    char* ctl = ring + PF * kStreamMaxThreads * CB;
+    float* ebuf = reinterpret_cast<float*>(ctl + kStreamTmaCtlBytes);
+    const int NT = blockDim.x;
+    const int tid = threadIdx.x;
+    const int strip = blockIdx.x % p.strips;
+    const int tile = blockIdx.x / p.strips;
+    const int x0 = strip * p.bx;
+    const int y0 = tile * p.by;
+    TmaRing tma;
+    tma.map = &map;
+    tma.bar0 = st_smem(ctl);
+    tma.abort = reinterpret_cast<volatile int*>(ctl + 8 * PF);
+    if (tid == 0) {
+        for (int i = 0; i < PF; ++i) st_bar_init(tma.bar0 + 8u * (unsigned)i, 1);
+        *tma.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < 2 * K * stream_buf_floats(R); i += NT) ebuf[i] = 0.f;
+    __syncthreads();
+
+    const int ny = (int)p.ny, nx = (int)p.nx;
+    const int ylast = min(y0 + p.by, ny);
+    const bool interior = y0 - R * K >= 0 && ylast + stream_rows_after(R, K) <= ny && x0 - p.H >= 0 &&
+                          x0 - p.H + 4 * NT <= nx;
+    const ParamWeights ws{p};
+    if (interior)
+        stream_tile<R, STAR, K, float, true, false, true>(p, ws, ring, ebuf, NT, tid, x0, y0, tma);
+    else
+        stream_tile<R, STAR, K, float, true, true, true>(p, ws, ring, ebuf, NT, tid, x0, y0, tma);
 }
 
 // Host-side handle of one instantiation.

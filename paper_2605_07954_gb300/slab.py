@@ -121,7 +121,7 @@ class SlabSweep:
                  device=None, **plan_options):
         import torch
         import torch.distributed as dist
-        from . import BOUNDARIES, COMPUTES, DTYPES, KERNELS
+        from . import BOUNDARIES, COMPUTES, DTYPES, KERNELS, LOADS
         if rank is None or world is None:
             if dist.is_available() and dist.is_initialized():
                 rank, world = dist.get_rank(group), dist.get_world_size(group)
@@ -140,7 +140,8 @@ class SlabSweep:
                                       int(plan_options.pop("tb_depth", 0)),
                                       int(plan_options.pop("threads", 0)),
                                       int(plan_options.pop("tile_rows", 0)),
-                                      int(bool(plan_options.pop("autotune", False))), 0, 0, 0)
+                                      int(bool(plan_options.pop("autotune", False))), 0, 0, 0,
+                                      LOADS[plan_options.pop("load", "auto")])
         if plan_options:
             raise TypeError(f"unknown options {sorted(plan_options)}")
         lib = _capi.load()

@@ -58,8 +58,9 @@ def test_rejects_null_and_bad_enums(lib):
     assert _create(lib, 8, 8, 1, bad)[0] == _capi.STENCIL_ERR_INVALID_ARG
     opt = _capi.stencil_options_t(0, 9, 0, 0, 0, 0)
     assert _create(lib, 8, 8, 1, w, opt=opt)[0] == _capi.STENCIL_ERR_INVALID_ARG
-    for field, value in (("compute", 5), ("kernel", 7), ("mma_n", -1), ("timeout_ms", -5),
-                         ("debug_withhold", 2)):
+    for field, value in (("compute", 6), ("kernel", 7), ("mma_n", -1), ("timeout_ms", -5),
+                         ("debug_withhold", 2), ("load", 3), ("load", -1),
+                         ("rank", -1), ("rank", 4)):
         opt = _capi.stencil_options_t()
         setattr(opt, field, value)
         assert _create(lib, 8, 8, 1, w, opt=opt)[0] == _capi.STENCIL_ERR_INVALID_ARG, field

@@ -126,6 +126,42 @@ def test_autograd_function_matches_adjoint(oracle):
     assert rel_l2(W.grad.numpy(), ref_w) <= 1e-4
 
 
+def test_autograd_loop_reuses_plans(oracle):
+    """A training loop: StencilFn with new weights every iteration.  Each
+    iteration's gradients match the oracle's, and after the first iteration no
+    device memory is taken (the cached plan and its adjoint scratch are reused
+    with the new weights)."""
+    from paper_2605_07954_gb300 import StencilFn
+    u0 = torch.from_numpy(inputs.field(96, 80)).cuda().requires_grad_()
+    target = torch.from_numpy(inputs.field(96, 80, stream=inputs.STREAM_TARGET)).cuda()
+    rng = np.random.default_rng(3)
+    free = []
+    for it in range(4):
+        Wn = rng.uniform(0.05, 0.2, size=(3, 3))
+        W = torch.from_numpy(Wn).requires_grad_()
+        u0.grad = None
+        uT = StencilFn.apply(u0, W, 16)
+        loss = 0.5 * ((uT - target) ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        gT = (uT.detach() - target).cpu().numpy().astype(np.float64)
+        ref_u, ref_w = oracle.adjoint_f64(u0.detach().cpu().numpy(), W.detach().numpy().astype(np.float32),
+                                          16, gT)
+        assert rel_l2(u0.grad.cpu().numpy(), ref_u) <= 1e-4, it
+        assert rel_l2(W.grad.numpy(), ref_w) <= 1e-4, it
+    assert free[-1] >= free[1], free
+
+
+def test_set_weights_keeps_the_footprint():
+    from paper_2605_07954_gb300 import Plan, StencilError
+    p = Plan(64, 64, inputs.heat_weights(0.2))
+    p.set_weights(inputs.heat_weights(0.1))  # still a 5-point star
+    with pytest.raises(StencilError):
+        p.set_weights(inputs.pattern_weights("box9"))  # a box: another kernel
+    p.close()
+
+
 def test_fullsize_heat_4096_T512_window(oracle):
     """The 4096^2, 512-step Heat workload: the corner window of dL/du0 against
     the FP64 oracle on its exact light cone, and the dot test at full size."""
