@@ -256,7 +256,9 @@ const char* stencil_residual_last_error(void);
  *   plan           an FP32 plan (other dtypes: STENCIL_ERR_UNSUPPORTED).
  *   u0, grad_uT    DEVICE, ny*nx FP32, only read.
  *   grad_u0        DEVICE, ny*nx FP32, written (may equal grad_uT).
- *   grad_w         DEVICE, (2r+1)^2 FP64, written; NULL to skip.  Every entry of the
+ *   grad_w         (2r+1)^2 FP64, written; NULL to skip.  DEVICE memory (asynchronous
+ *                  like the rest), or HOST memory (pageable or pinned: the call then
+ *                  synchronises `stream` before it returns).  Every entry of the
  *                  square is returned, off-footprint ones included.
  *   ckpt_interval  steps between checkpoints; 0 = ceil(sqrt(T)).  The result does
  *                  not depend on it (same bits).

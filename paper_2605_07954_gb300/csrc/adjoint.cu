@@ -485,7 +485,7 @@ stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const voi
     // Buffers: nseg checkpoints, sgm segment states, two adjoint grids.
     AdjScratch* sc = nullptr;
     const size_t grids = (size_t)nseg + (size_t)sgm + 2;
-    s = adj_scratch(plan, grids, bytes, (size_t)tiles * D * D, &sc);
+    s = adj_scratch(plan, grids, bytes, (size_t)(tiles + 1) * D * D, &sc);
     if (s != STENCIL_OK) return s;
     float* ckpt = sc->base;
     float* seg = sc->base + (size_t)nseg * n;
@@ -528,8 +528,19 @@ stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const voi
     ACK(cudaMemcpyAsync(grad_u0, lam[cur], bytes, cudaMemcpyDeviceToDevice, st));
     if (grad_w) {
         const int taps = D * D;
-        reduce_partials_kernel<<<taps, 256, 0, st>>>(partials, tiles, taps, grad_w);
+        // grad_w may be host memory: then the sums go to the tail of the
+        // partials scratch first and are copied back, synchronising `stream`.
+        cudaPointerAttributes pa{};
+        const bool host = cudaPointerGetAttributes(&pa, grad_w) != cudaSuccess ||
+                          pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
+        (void)cudaGetLastError();
+        double* dst = host ? partials + (size_t)tiles * D * D : grad_w;
+        reduce_partials_kernel<<<taps, 256, 0, st>>>(partials, tiles, taps, dst);
         ACK(cudaGetLastError());
+        if (host) {
+            ACK(cudaMemcpyAsync(grad_w, dst, sizeof(double) * taps, cudaMemcpyDeviceToHost, st));
+            ACK(cudaStreamSynchronize(st));
+        }
     }
     return STENCIL_OK;
 }

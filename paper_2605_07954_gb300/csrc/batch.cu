@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
     constexpr int CB = 4 * (int)sizeof(TS);
     extern __shared__ float4 smem_f4[];
     char* ring = reinterpret_cast<char*>(smem_f4);
-    float* ebuf = reinterpret_cast<float*>(ring + kStreamPrefetch * kStreamMaxThreads * CB);
+    float* ebuf = reinterpret_cast<float*>(ring + stream_prefetch(K) * (int)blockDim.x * CB);
     __shared__ int s_item;
     const int NT = blockDim.x;
     const int tid = threadIdx.x;
@@ -407,7 +407,7 @@ stencil_status_t build_schedule(stencil_batch* b, int k, int threads, int tile_r
     for (auto& L : b->launches) {
         L.fn = batch_kernel(L.R, L.depth, b->dtype);
         if (!L.fn) return bfail(STENCIL_ERR_UNSUPPORTED, "no batched kernel for this depth");
-        L.smem = stream_smem_bytes(L.R, L.depth, (int)b->elem, true);
+        L.smem = stream_smem_bytes(L.R, L.depth, (int)b->elem, true, false, kStreamMaxThreads);
         BCK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem));
         int per_sm = 0;
         BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.fn, threads, L.smem));

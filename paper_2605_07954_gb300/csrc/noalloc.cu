@@ -123,7 +123,7 @@ stencil_status_t launch_depth(const Geometry& g, const StreamParams& base, int R
     sp.vec = (sp.nx % 4 == 0) && ((uintptr_t)src % vb == 0) && ((uintptr_t)dst % vb == 0);
     StreamKernelRef r = kernel_for(R, star, depth, dtype, sp.vec);
     if (!r.fn) return nfail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for this depth");
-    const int smem = stream_smem_bytes(R, depth, elem, sp.vec != 0);
+    const int smem = stream_smem_bytes(R, depth, elem, sp.vec != 0, false, g.nt);
     NCK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     void* args[] = {&sp};
     NCK(cudaLaunchKernel(r.fn, dim3((unsigned)(g.strips * g.tiles_y)), dim3((unsigned)g.nt), args,
@@ -199,7 +199,7 @@ stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const f
         const int vec = nx % 4 == 0;
         StreamKernelRef r = kernel_for(radius, star, k, dtype, vec);
         if (!r.fn) return nfail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for this shape");
-        const int smem = stream_smem_bytes(radius, k, elem, vec != 0);
+        const int smem = stream_smem_bytes(radius, k, elem, vec != 0, false, g.nt);
         NCK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r.fn, g.nt, smem));
     }

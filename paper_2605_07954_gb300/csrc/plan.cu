@@ -193,17 +193,19 @@ static StreamKernelRef stream_tma_kernel(int R, int star, int k) {
 
 // The depth-`depth` streaming kernel (TMA-fed, VEC or element-wise variant),
 // with its shared-memory attribute set on first use.
+// `smem` receives the dynamic shared memory of a launch with CTAs of `nt`
+// threads; the kernel's attribute allows the largest CTA.
 static stencil_status_t stream_fn(stencil_plan* p, int depth, int vec, const void** fn, int* smem,
-                                  int tma = -1) {
-    if (tma < 0) tma = p->tma;
+                                  int tma, int nt) {
     tma = tma && vec;
     StreamKernelRef r = tma ? stream_tma_kernel(p->R, p->star, depth)
                             : stream_kernel(p->R, p->star, depth, p->dtype, vec);
     if (!r.fn) return fail(STENCIL_ERR_UNSUPPORTED, "no streaming kernel for depth " + std::to_string(depth));
-    *smem = stream_smem_bytes(p->R, depth, (int)p->elem, vec != 0, tma != 0);
+    *smem = stream_smem_bytes(p->R, depth, (int)p->elem, vec != 0, tma != 0, nt);
     const unsigned bit = 1u << (2 * depth + (vec ? 1 : 0) + (tma ? 16 : 0));
     if (!(p->smem_set & bit)) {
-        CK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
+        CK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                stream_smem_bytes(p->R, depth, (int)p->elem, vec != 0, tma != 0, kStreamMaxThreads)));
         p->smem_set |= bit;
     }
     *fn = r.fn;
@@ -255,16 +257,16 @@ static stencil_status_t configure_stream(stencil_plan* p, int k, int threads, in
     if (threads < 32 || threads > kStreamMaxThreads || threads % 32)
         return fail(STENCIL_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..256");
     const int vec = p->nx % 4 == 0;
-    const void* fn = nullptr;
-    int smem = 0;
-    stencil_status_t st = stream_fn(p, k, vec, &fn, &smem);
-    if (st != STENCIL_OK) return st;
     const int H = (p->R * k + 3) / 4 * 4;
     const int bx_max = 4 * threads - 2 * H;
     if (bx_max < 4) return fail(STENCIL_ERR_UNSUPPORTED, "CTA too narrow for this depth");
     const int64_t strips = ceil_div(p->nx, bx_max);
     const int bx = (int)(ceil_div(ceil_div(p->nx, strips), 4) * 4);
     const int nt = (int)(ceil_div(ceil_div(bx + 2 * H, 4), 32) * 32);
+    const void* fn = nullptr;
+    int smem = 0;
+    stencil_status_t st = stream_fn(p, k, vec, &fn, &smem, p->tma, nt);
+    if (st != STENCIL_OK) return st;
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
     if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "streaming kernel does not fit on an SM");
@@ -574,7 +576,7 @@ static stencil_status_t launch_once(stencil_plan* p, const void* src, void* dst,
     // The TMA-fed kernel when the plan uses it and this source has a tensor
     // map (16-byte aligned); otherwise the cp.async kernel, same arithmetic.
     const int tma = p->tma && sp.vec && stream_tensor_map(&map, src, p->ny, p->nx);
-    stencil_status_t s = stream_fn(p, nlev, sp.vec, &fn, &smem, tma);
+    stencil_status_t s = stream_fn(p, nlev, sp.vec, &fn, &smem, tma, p->threads);
     if (s != STENCIL_OK) return s;
     if (tma) {
         void* args[] = {&map, &sp};

@@ -60,7 +60,11 @@
 namespace gbst {
 
 constexpr int kStreamMaxThreads = 256;
-constexpr int kStreamPrefetch = 4;  // rows in flight per thread (power of 2)
+
+// Input rows in flight per thread (a power of 2).  Measured on GB300: 8 rows
+// for K <= 2 gained nothing for the 13-point star and cost the 49-point box at
+// 256-thread CTAs an occupancy step (its ring no longer fit twice per SM).
+__host__ __device__ constexpr int stream_prefetch(int) { return 4; }
 
 // Floats of one (level, parity) edge buffer, sized for the largest CTA so
 // that every shared-memory offset is a compile-time constant.
@@ -73,10 +77,12 @@ constexpr int kStreamTmaCtlBytes = 128;
 // Columns of one TMA box (one 512-byte piece of an FP32 ring row).
 constexpr int kStreamTmaBox = 128;
 
-// Dynamic shared memory of a launch: the input ring (VEC only), the TMA
+// Dynamic shared memory of a launch with CTAs of `nt` threads: the input ring
+// (VEC only; one slot of nt 4-element chunks per row in flight), the TMA
 // control block (TMA-fed kernels) and 2K edge buffers.
-__host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes, bool vec, bool tma = false) {
-    return (vec ? kStreamPrefetch * kStreamMaxThreads * 4 * elem_bytes : 0) + (tma ? kStreamTmaCtlBytes : 0) +
+__host__ __device__ constexpr int stream_smem_bytes(int R, int K, int elem_bytes, bool vec, bool tma = false,
+                                                    int nt = kStreamMaxThreads) {
+    return (vec ? stream_prefetch(K) * nt * 4 * elem_bytes : 0) + (tma ? kStreamTmaCtlBytes : 0) +
            2 * K * stream_buf_floats(R) * 4;
 }
 
@@ -455,8 +461,9 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                                             TmaRing tma = TmaRing{}) {
     constexpr int D = 2 * R + 1;
     constexpr int SZ = stream_buf_floats(R);
-    constexpr int PF = kStreamPrefetch;
+    constexpr int PF = stream_prefetch(K);
     constexpr int CB = 4 * (int)sizeof(TS);  // bytes of one 4-column chunk
+    const int SLOT = NT * CB;                // bytes of one ring slot (one row of the strip)
     const int ny = (int)p.ny, nx = (int)p.nx;
     const size_t ld = (size_t)p.ld;
     const int c0 = x0 - p.H + 4 * tid;  // this thread's first column
@@ -503,7 +510,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
             if (tid < nbox && s < nsteps && !*tma.abort) {
                 const int slot = s & (PF - 1);
                 const unsigned bar = tma.bar0 + 8u * (unsigned)slot;
-                const unsigned dst = st_smem(ring + slot * (kStreamMaxThreads * CB)) + (unsigned)(tid * kStreamTmaBox * 4);
+                const unsigned dst = st_smem(ring + slot * SLOT) + (unsigned)(tid * kStreamTmaBox * 4);
                 const int xs = x0 - p.H + tid * kStreamTmaBox;
                 // the copy's first column must be 16-byte aligned, and so must its
                 // destination (128 bytes: every box starts on a 512-byte boundary)
@@ -538,7 +545,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
         } else {
             src = ok ? my_src + (size_t)s * ld : gin;
         }
-        cp_async<CB>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), src, ok);
+        cp_async<CB>(my_ring + (s & (PF - 1)) * SLOT, src, ok);
         cp_async_commit();
     };
 
@@ -562,11 +569,11 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                 issue_row(s + PF - 1);
                 st_wait(tma.bar0 + 8u * (unsigned)(s & (PF - 1)), (unsigned)((s / PF) & 1), tma.abort, p.status,
                         p.wait_ns);
-                smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), cur);
+                smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * SLOT, cur);
             } else if constexpr (VEC) {
                 issue_row(s + PF - 1);
                 cp_async_wait<PF - 1>();
-                smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * (kStreamMaxThreads * CB), cur);
+                smem_chunk_to_f32<TS>(my_ring + (s & (PF - 1)) * SLOT, cur);
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) { cur[e] = nreg0[e]; nreg0[e] = nreg1[e]; }
@@ -734,12 +741,12 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
 template <int R, bool STAR, int K, typename TS, bool VEC>
 __global__ void __launch_bounds__(kStreamMaxThreads)
     sweep_stream_kernel(const __grid_constant__ StreamParams p) {
-    constexpr int PF = kStreamPrefetch;
+    constexpr int PF = stream_prefetch(K);
     constexpr int CB = 4 * (int)sizeof(TS);
     extern __shared__ float4 smem_f4[];
-    char* ring = reinterpret_cast<char*>(smem_f4);
-    float* ebuf = reinterpret_cast<float*>(ring + (VEC ? PF * kStreamMaxThreads * CB : 0));
     const int NT = blockDim.x;
+    char* ring = reinterpret_cast<char*>(smem_f4);
+    float* ebuf = reinterpret_cast<float*>(ring + (VEC ? PF * NT * CB : 0));
     const int tid = threadIdx.x;
     const int strip = blockIdx.x % p.strips;
     const int tile = blockIdx.x / p.strips;
@@ -768,13 +775,13 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
 template <int R, bool STAR, int K>
 __global__ void __launch_bounds__(kStreamMaxThreads)
     sweep_stream_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ StreamParams p) {
-    constexpr int PF = kStreamPrefetch;
+    constexpr int PF = stream_prefetch(K);
     constexpr int CB = 16;
     extern __shared__ __align__(1024) float4 smem_tma[];
-    char* ring = reinterpret_cast<char*>(smem_tma);
-    char* ctl = ring + PF * kStreamMaxThreads * CB;
-    float* ebuf = reinterpret_cast<float*>(ctl + kStreamTmaCtlBytes);
     const int NT = blockDim.x;
+    char* ring = reinterpret_cast<char*>(smem_tma);
+    char* ctl = ring + PF * NT * CB;
+    float* ebuf = reinterpret_cast<float*>(ctl + kStreamTmaCtlBytes);
     const int tid = threadIdx.x;
     const int strip = blockIdx.x % p.strips;
     const int tile = blockIdx.x / p.strips;

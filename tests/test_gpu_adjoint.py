@@ -153,6 +153,28 @@ def test_autograd_loop_reuses_plans(oracle):
     assert free[-1] >= free[1], free
 
 
+def test_weight_gradient_into_host_memory():
+    """grad_w may be host memory: the call synchronises and writes the same
+    values as into device memory."""
+    import ctypes
+    from paper_2605_07954_gb300 import Plan, _capi
+    W = inputs.pattern_weights("box9")
+    u0 = torch.from_numpy(inputs.field(70, 90)).cuda()
+    gT = torch.from_numpy(inputs.field(70, 90, stream=inputs.STREAM_TARGET)).cuda()
+    p = Plan(70, 90, W)
+    lib = _capi.load()
+    st = torch.cuda.current_stream().cuda_stream
+    gu = torch.empty_like(u0)
+    gw_dev = torch.empty((3, 3), dtype=torch.float64, device="cuda")
+    assert lib.stencil_adjoint(p.handle, u0.data_ptr(), gT.data_ptr(), 12, gu.data_ptr(),
+                               gw_dev.data_ptr(), 0, st) == 0
+    for host in (np.zeros(9), torch.zeros(9, dtype=torch.float64).pin_memory().numpy()):
+        assert lib.stencil_adjoint(p.handle, u0.data_ptr(), gT.data_ptr(), 12, gu.data_ptr(),
+                                   host.ctypes.data_as(ctypes.c_void_p), 0, st) == 0
+        assert np.array_equal(host, gw_dev.cpu().numpy().ravel())
+    p.close()
+
+
 def test_set_weights_keeps_the_footprint():
     from paper_2605_07954_gb300 import Plan, StencilError
     p = Plan(64, 64, inputs.heat_weights(0.2))
