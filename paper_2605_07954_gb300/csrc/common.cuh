@@ -42,6 +42,7 @@ struct StreamParams {
     unsigned* status;   // TMA-fed kernels: device status word (bounded waits), else unused
     long long wait_ns;  // TMA-fed kernels: limit of each wait for a row
     int debug_withhold; // TMA-fed kernels, test hook: CTA 0 expects 16 bytes its first row never brings
+    void* lvl_out[8];   // all-states kernels: time level l+1 (l < nlev-1) is also stored to lvl_out[l]
     Weights w;
     WeightPairs w2;
 };

@@ -30,6 +30,7 @@ GBST_DECL_STREAM(1, f32) GBST_DECL_STREAM(1, bf16) GBST_DECL_STREAM(1, f16)
 GBST_DECL_STREAM(2, f32) GBST_DECL_STREAM(2, bf16) GBST_DECL_STREAM(2, f16)
 GBST_DECL_STREAM(3, f32) GBST_DECL_STREAM(3, bf16) GBST_DECL_STREAM(3, f16)
 #undef GBST_DECL_STREAM
+StreamKernelRef get_stream_states_kernel(int R, int star, int k);
 StreamKernelRef get_stream_tma_kernel_r1(int star, int k);
 StreamKernelRef get_stream_tma_kernel_r2(int star, int k);
 StreamKernelRef get_stream_tma_kernel_r3(int star, int k);
@@ -130,6 +131,8 @@ void plan_weights(const stencil_plan_t* p, float* w) {
 }
 void** plan_aux_slot(stencil_plan_t* p, int id) { return &p->aux[id]; }
 void plan_set_aux_free(stencil_plan_t* p, int id, void (*freer)(void*)) { p->aux_free[id] = freer; }
+stencil_status_t plan_run_states(stencil_plan_t* p, const void* in, float* const* outs, int64_t n,
+                                 cudaStream_t st);
 }  // namespace gbst
 
 static size_t elem_size(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
@@ -606,6 +609,90 @@ static std::vector<int> launch_depths(const stencil_plan* p, int64_t T) {
     }
     return d;
 }
+
+// ---- all states of a run (the adjoint's segment recomputation) ------------------------
+//
+// outs[i] = u_{i+1} for i < n, from u_0 = in: launches of the all-states
+// kernels (depths 8 / 4 / 2 / 1 as available), each reading the last state the
+// previous launch wrote and storing every level.  FP32 plans whose rows are
+// 16-byte aligned; anything else runs one single-step stencil_run per state.
+// Each state is the same bits as stencil_run produces (same arithmetic per
+// point, independent of the launch depths).
+
+namespace gbst {
+stencil_status_t plan_run_states(stencil_plan_t* p, const void* in, float* const* outs, int64_t n,
+                                 cudaStream_t st) {
+    bool fused = p->dtype == STENCIL_F32 && p->nx % 4 == 0 && (uintptr_t)in % 16 == 0;
+    for (int64_t i = 0; i < n && fused; ++i) fused = (uintptr_t)outs[i] % 16 == 0;
+    if (!fused) {
+        const void* src = in;
+        for (int64_t i = 0; i < n; ++i) {
+            stencil_status_t s = stencil_run(p, src, outs[i], 1, st);
+            if (s != STENCIL_OK) return s;
+            src = outs[i];
+        }
+        return STENCIL_OK;
+    }
+    const int threads = 128;
+    const void* src = in;
+    for (int64_t i = 0; i < n;) {
+        int d = 8;
+        StreamKernelRef r{nullptr, 0};
+        for (; d >= 1; d /= 2) {
+            if (d > n - i) continue;
+            r = get_stream_states_kernel(p->R, p->star, d);
+            if (r.fn) break;
+        }
+        if (!r.fn) return fail(STENCIL_ERR_UNSUPPORTED, "no all-states kernel");
+        const int H = (p->R * d + 3) / 4 * 4;
+        const int64_t strips = ceil_div(p->nx, 4 * threads - 2 * H);
+        const int bx = (int)(ceil_div(ceil_div(p->nx, strips), 4) * 4);
+        const int nt = (int)(ceil_div(ceil_div(bx + 2 * H, 4), 32) * 32);
+        const int smem = stream_smem_bytes(p->R, d, 4, true, false, nt);
+        const unsigned bit = 1u << d;
+        static std::mutex mu;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            static unsigned set_bits[3][2] = {};
+            if (!(set_bits[p->R - 1][p->star] & bit)) {
+                CK(cudaFuncSetAttribute(r.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        stream_smem_bytes(p->R, d, 4, true, false, kStreamMaxThreads)));
+                set_bits[p->R - 1][p->star] |= bit;
+            }
+        }
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r.fn, nt, smem));
+        if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "all-states kernel does not fit on an SM");
+        const int64_t want = std::max<int64_t>(1, (int64_t)per_sm * p->sms / strips);
+        const int64_t by_min = std::max<int64_t>(8, 4LL * p->R * d);
+        int64_t tiles_y = std::max<int64_t>(1, std::min<int64_t>(want, ceil_div(p->ny, by_min)));
+        const int by = (int)ceil_div(p->ny, tiles_y);
+        tiles_y = ceil_div(p->ny, by);
+        StreamParams sp{};
+        sp.in = src;
+        sp.out = outs[i + d - 1];
+        sp.ny = p->ny;
+        sp.nx = p->nx;
+        sp.ld = p->nx;
+        sp.nlev = d;
+        sp.H = H;
+        sp.bx = bx;
+        sp.by = by;
+        sp.strips = (int)strips;
+        sp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
+        sp.vec = 1;
+        sp.status = p->status;
+        sp.w = p->w;
+        for (int t = 0; t < kMaxTaps; ++t) sp.w2.w2[t] = make_float2(p->w.w[t], p->w.w[t]);
+        for (int l = 0; l < d - 1; ++l) sp.lvl_out[l] = outs[i + l];
+        void* args[] = {&sp};
+        CK(cudaLaunchKernel(r.fn, dim3((unsigned)(strips * tiles_y)), dim3((unsigned)nt), args, (size_t)smem, st));
+        src = outs[i + d - 1];
+        i += d;
+    }
+    return STENCIL_OK;
+}
+}  // namespace gbst
 
 // ---- autotuning ---------------------------------------------------------------------
 //

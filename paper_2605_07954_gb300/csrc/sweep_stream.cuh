@@ -455,7 +455,8 @@ __host__ __device__ constexpr int stream_rows_after(int R, int K) {
 // row (zero rule, edge tiles) and, at the top level, stores it.  Per output the
 // products are still added row by row (dy = -R .. R), own columns before
 // neighbour columns, so the result does not depend on the schedule or on K.
-template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, bool TMA = false, class WS>
+template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, bool TMA = false, bool ALL = false,
+          class WS>
 __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws, char* ring,
                                             float* ebuf, int NT, int tid, int x0, int y0,
                                             TmaRing tma = TmaRing{}) {
@@ -610,6 +611,12 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                             if (row_out || !col_in[3]) Pb.y = 0.f;
                         }
                     }
+                    if constexpr (ALL) {
+                        const int yo = ybeg - (l + 1) * R + s;
+                        if (l < K - 1 && store_chunk && yo >= y0 && yo < ylast)
+                            Storage<TS>::store4(static_cast<TS*>(p.lvl_out[l]) + (size_t)yo * ld + c0,
+                                                make_float4(Pa.x, Pb.x, Pa.y, Pb.y));
+                    }
                 }
                 const int yo = ybeg - R * K + s;
                 if (store_chunk && yo >= y0 && yo < ylast) {
@@ -710,6 +717,14 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                         if (row_out || !col_in[3]) A1.y = 0.f;
                     }
                 }
+                if constexpr (ALL) {
+                    const int yo = ybeg + s - l * (R + 1) - R;
+                    if (l < K - 1 && store_chunk && yo >= y0 && yo < ylast) {
+                        const float2 A0 = acc[l][cdone][0], A1 = acc[l][cdone][1];
+                        Storage<TS>::store4(static_cast<TS*>(p.lvl_out[l]) + (size_t)yo * ld + c0,
+                                            make_float4(A0.x, A0.y, A1.x, A1.y));
+                    }
+                }
                 if (l == K - 1) {
                     const int yo = ybeg + s - (K - 1) * (R + 1) - R;
                     if (store_chunk && yo >= y0 && yo < ylast) {
@@ -738,7 +753,10 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
     }
 }
 
-template <int R, bool STAR, int K, typename TS, bool VEC>
+// ALL: every time level of the launch is stored (level l+1 to p.lvl_out[l],
+// the last to p.out), for callers that need each state (the adjoint's
+// recomputation of a segment); VEC kernels only.
+template <int R, bool STAR, int K, typename TS, bool VEC, bool ALL = false>
 __global__ void __launch_bounds__(kStreamMaxThreads)
     sweep_stream_kernel(const __grid_constant__ StreamParams p) {
     constexpr int PF = stream_prefetch(K);
@@ -764,9 +782,9 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
                           x0 - p.H >= 0 && x0 - p.H + 4 * NT <= nx;
     const ParamWeights ws{p};
     if (interior)
-        stream_tile<R, STAR, K, TS, VEC, false>(p, ws, ring, ebuf, NT, tid, x0, y0);
+        stream_tile<R, STAR, K, TS, VEC, false, false, ALL>(p, ws, ring, ebuf, NT, tid, x0, y0);
     else
-        stream_tile<R, STAR, K, TS, VEC, true>(p, ws, ring, ebuf, NT, tid, x0, y0);
+        stream_tile<R, STAR, K, TS, VEC, true, false, ALL>(p, ws, ring, ebuf, NT, tid, x0, y0);
 }
 
 // The same sweep with the input rows brought in by the tensor-memory-access
