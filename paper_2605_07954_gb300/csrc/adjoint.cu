@@ -21,9 +21,8 @@
 // FP64 partial.  Tile t of a launch is always CTA t and launches are ordered,
 // so each partial sums its steps in a fixed order; a last kernel sums the
 // partials over tiles in a fixed order.  The gradient is deterministic.
-// adjoint_stream_kernel does the same step with rows streamed through a
-// per-warp cp.async ring and registers instead of a staged tile (radius 1,
-// widths a multiple of 4).
+// adjoint_stream_kernel does the same step with rows streamed through
+// registers instead of a staged tile (radius 1, widths a multiple of 4).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -202,22 +201,23 @@ __global__ void __launch_bounds__(256)
 // 4 adjacent columns per lane, and walks down the rows holding the last 2R+1
 // rows of lambda_{t+1} and of u_t in registers, each extended by R halo
 // columns: the neighbouring lanes' columns by shuffles, the strip's outer
-// columns loaded by lanes 0 and 31.  Rows arrive through a warp-private
-// shared-memory ring filled by cp.async kAdsAhead rows before their use
-// (each thread copies, and later reads, only its own 16-byte chunk and halo
-// words, so no barrier is needed): many rows in flight without holding them in
-// registers.  Per output the lambda update is adjoint_step_kernel's, in the
-// same order (bit-identical lambda); each thread adds its gradient products
-// row by row, column by column, then the CTA reduces them in a fixed order
-// into its FP64 partial.  Measured on GB300 (Heat 4096^2): the staged-tile step
-// is issue-bound (62.3 us per reverse step); rows held two ahead in registers
-// gave 47.3 us, load-latency bound at ~17 warps per SM.
+// columns loaded by lanes 0 and 31.  Rows are loaded as 16-byte chunks
+// kAdsAhead rows before their use.  Nothing goes through shared memory on the
+// way, so the loads of one warp overlap the arithmetic of the others, where
+// adjoint_step_kernel stages a whole tile before it computes.  Per output the
+// lambda update is adjoint_step_kernel's, in the same order (bit-identical
+// lambda); each thread adds its gradient products row by row, column by
+// column, then the CTA reduces them in a fixed order into its FP64 partial.
+// Measured on GB300 (Heat 4096^2): 47.3 us per reverse step against 62.3 for
+// the staged-tile step, which is issue-bound (~128 instructions per output).
+// Unrolling the whole row walk (instruction-cache misses: 69 us), holding
+// four rows in flight instead of two (more registers, fewer warps: 58 us), or
+// bringing the rows through a per-warp cp.async ring six rows ahead (79
+// registers; the backward pass 5 % slower) were slower.
 constexpr int kAdsWarps = 4;    // warps per CTA, stacked vertically
 constexpr int kAdsRows = 16;    // output rows per warp
 constexpr int kAdsCols = 128;   // strip width (32 lanes x 4 columns)
-constexpr int kAdsAhead = 6;    // rows copied ahead of their use
-constexpr int kAdsSlots = 8;    // ring slots per warp (> kAdsAhead, power of 2)
-constexpr int kAdsArr = 544;    // bytes per array and slot: 32 x 16-byte chunks + halo words
+constexpr int kAdsAhead = 2;    // rows loaded ahead of their use
 
 template <int R>
 struct AdsRow {
@@ -225,22 +225,13 @@ struct AdsRow {
     float h[R];   // lane 0: columns x0 - R .. x0 - 1; lane 31: x0 + 128 .. x0 + 127 + R
 };
 
-__device__ __forceinline__ void ads_cp16(void* dst, const void* src, bool ok) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0));
-}
-__device__ __forceinline__ void ads_cp4(void* dst, const void* src, bool ok) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0));
-}
-
-// Copy grid row y of g, as lane `lane` of the strip at x0 needs it, into the
-// array area `dst` of a ring slot; zero outside the grid, or wrapped.
-// c = x0 + 4 lane is a multiple of 4 and nx % 4 == 0, so a chunk lies wholly
-// inside or wholly outside the grid, and its wrapped image is again an aligned chunk.
+// Grid row y of g as lane `lane` of the strip at x0 needs it; zero outside the
+// grid, or wrapped.  c = x0 + 4 lane is a multiple of 4 and nx % 4 == 0, so a
+// chunk lies wholly inside or wholly outside the grid, and its wrapped image
+// is again an aligned chunk.
 template <int R>
-__device__ __forceinline__ void ads_issue(char* dst, const float* __restrict__ g, int y, int c, int x0, int lane,
-                                          int ny, int nx, bool periodic) {
+__device__ __forceinline__ void ads_load(AdsRow<R>& a, const float* __restrict__ g, int y, int c, int x0,
+                                         int lane, int ny, int nx, bool periodic) {
     bool rok = true;
     if (periodic) {
         if (y < 0 || y >= ny) y = (y % ny + ny) % ny;
@@ -255,29 +246,18 @@ __device__ __forceinline__ void ads_issue(char* dst, const float* __restrict__ g
     } else {
         cok = cc < nx;
     }
-    ads_cp16(dst + lane * 16, rok && cok ? row + cc : g, rok && cok);
-    if (lane == 0 || lane == 31) {
+    a.v = rok && cok ? __ldg(reinterpret_cast<const float4*>(row + cc)) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            int xc = lane == 0 ? x0 - R + i : x0 + kAdsCols + i;
-            bool ok = rok;
-            if (periodic) {
-                if (xc < 0 || xc >= nx) xc = (xc % nx + nx) % nx;
-            } else {
-                ok = ok && xc >= 0 && xc < nx;
-            }
-            ads_cp4(dst + 512 + (lane == 0 ? i : R + i) * 4, ok ? row + xc : g, ok);
+    for (int i = 0; i < R; ++i) {
+        int xc = lane == 0 ? x0 - R + i : x0 + kAdsCols + i;
+        bool ok = rok && (lane == 0 || lane == 31);
+        if (periodic) {
+            if (xc < 0 || xc >= nx) xc = (xc % nx + nx) % nx;
+        } else {
+            ok = ok && xc >= 0 && xc < nx;
         }
+        a.h[i] = ok ? __ldg(row + xc) : 0.f;
     }
-}
-
-template <int R>
-__device__ __forceinline__ void ads_fetch(AdsRow<R>& a, const char* src, int lane) {
-    a.v = *reinterpret_cast<const float4*>(src + lane * 16);
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-        a.h[i] = lane == 0 ? *reinterpret_cast<const float*>(src + 512 + i * 4)
-                           : (lane == 31 ? *reinterpret_cast<const float*>(src + 512 + (R + i) * 4) : 0.f);
 }
 
 // e[k] = column c - R + k of the row, k in [0, 4 + 2R).
@@ -302,11 +282,9 @@ __global__ void __launch_bounds__(kAdsWarps * 32)
                           int periodic, Weights w, int tiles_x) {
     constexpr int D = 2 * R + 1, E = 4 + 2 * R;
     constexpr int NR = kAdsRows + 2 * R;  // rows walked: yb - R .. yb + kAdsRows - 1 + R
-    static_assert(NR % D == 0, "window indices are static within a group of D rows");
-    static_assert(kAdsSlots > kAdsAhead && (kAdsSlots & (kAdsSlots - 1)) == 0, "ring");
-    static_assert(512 + 2 * R * 4 <= kAdsArr && kAdsArr % 16 == 0, "ring slot layout");
+    constexpr int RING = kAdsAhead + 1;
+    static_assert(RING == D && NR % D == 0, "ring and window indices are static within a group of D rows");
     __shared__ float red[kAdsWarps][D * D];
-    __shared__ __align__(16) char ring[kAdsWarps][kAdsSlots][2][kAdsArr];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x0 = (blockIdx.x % tiles_x) * kAdsCols;
     const int yb = (blockIdx.x / tiles_x) * (kAdsWarps * kAdsRows) + warp * kAdsRows;
@@ -314,39 +292,29 @@ __global__ void __launch_bounds__(kAdsWarps * 32)
     const bool per = periodic != 0;
     const bool col_ok = c < nx;
 
-    float el[D][E], eu[D][E];  // extended rows, window slot = row index % D
+    AdsRow<R> ra[RING], rb[RING];  // loaded rows of lambda_{t+1} and u_t, ring by row index
+    float el[D][E], eu[D][E];      // extended rows, window slot = row index % D
     float g[D * D];
 #pragma unroll
     for (int k = 0; k < D * D; ++k) g[k] = 0.f;
 #pragma unroll
     for (int i = 0; i < kAdsAhead; ++i) {
-        ads_issue<R>(ring[warp][i][0], lam_in, yb - R + i, c, x0, lane, ny, nx, per);
-        ads_issue<R>(ring[warp][i][1], u, yb - R + i, c, x0, lane, ny, nx, per);
-        asm volatile("cp.async.commit_group;\n" ::);
+        ads_load<R>(ra[i], lam_in, yb - R + i, c, x0, lane, ny, nx, per);
+        ads_load<R>(rb[i], u, yb - R + i, c, x0, lane, ny, nx, per);
     }
     // A rolled loop over groups of D rows (a fully unrolled walk overflows the
-    // instruction cache); inside a group every window index is static.
+    // instruction cache); inside a group every ring and window index is static.
 #pragma unroll 1
     for (int s0 = 0; s0 < NR; s0 += D) {
 #pragma unroll
         for (int jj = 0; jj < D; ++jj) {
             const int i = s0 + jj;
             if (i + kAdsAhead < NR) {
-                char* dst = ring[warp][(i + kAdsAhead) & (kAdsSlots - 1)][0];
-                ads_issue<R>(dst, lam_in, yb - R + i + kAdsAhead, c, x0, lane, ny, nx, per);
-                ads_issue<R>(dst + kAdsArr, u, yb - R + i + kAdsAhead, c, x0, lane, ny, nx, per);
+                ads_load<R>(ra[(jj + kAdsAhead) % RING], lam_in, yb - R + i + kAdsAhead, c, x0, lane, ny, nx, per);
+                ads_load<R>(rb[(jj + kAdsAhead) % RING], u, yb - R + i + kAdsAhead, c, x0, lane, ny, nx, per);
             }
-            asm volatile("cp.async.commit_group;\n" ::);
-            // row i's copies are complete once at most kAdsAhead later groups are pending
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(kAdsAhead));
-            {
-                AdsRow<R> ra, rb;
-                const char* src = ring[warp][i & (kAdsSlots - 1)][0];
-                ads_fetch<R>(ra, src, lane);
-                ads_fetch<R>(rb, src + kAdsArr, lane);
-                ads_extend<R>(ra, el[jj], lane);
-                ads_extend<R>(rb, eu[jj], lane);
-            }
+            ads_extend<R>(ra[jj % RING], el[jj], lane);
+            ads_extend<R>(rb[jj % RING], eu[jj], lane);
             // output row o = yb + k, k = i - 2R; window slot (k + m) % D holds grid row o - R + m
             const int k = i - 2 * R, o = yb + k;
             if (k < 0 || o >= ny || !col_ok) continue;
@@ -375,7 +343,6 @@ __global__ void __launch_bounds__(kAdsWarps * 32)
                 make_float4(res[0], res[1], res[2], res[3]);
         }
     }
-    asm volatile("cp.async.wait_group 0;\n" ::);
     // Fixed-order reduction: butterfly within each warp, then the warps in order.
 #pragma unroll
     for (int k = 0; k < D * D; ++k) {
