@@ -753,11 +753,30 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
     }
 }
 
+// Minimum resident 256-thread CTAs per SM the compiler must allow for (2: at
+// most 128 registers a thread, 3: 85; 0: no such bound, the compiler's own
+// choice, which differs from an explicit 1).  Measured on GB300 at 8192^2 with
+// per-instantiation register caps (same bits in every case): a 128-register cap
+// lifts the 5-point star at K = 8 from 2359 to 2731 GStencil/s, the 9-point box
+// at K = 6 from 1770 to 1842, the 13-point star at K = 3 / 4 from 1108 / 844 to
+// 1172 / 971 (it fits 4 CTAs instead of 3 / 2), the 49-point box at K = 2 from
+// 388 to 398; an 85-register cap lifts the 49-point box at K = 1 from 335 to
+// 353.  The 9-point box at K = 8 and the 13-point star at K = 2 are fastest
+// uncapped.
+__host__ __device__ constexpr int stream_min_blocks(int R, bool STAR, int K) {
+    return (R == 1 && STAR && K >= 6) ? 2
+         : (R == 1 && !STAR && K == 6) ? 2
+         : (R == 3 && STAR && K >= 3) ? 2
+         : (R == 3 && !STAR && K == 2) ? 2
+         : (R == 3 && !STAR && K == 1) ? 3
+         : 0;
+}
+
 // ALL: every time level of the launch is stored (level l+1 to p.lvl_out[l],
 // the last to p.out), for callers that need each state (the adjoint's
 // recomputation of a segment); VEC kernels only.
 template <int R, bool STAR, int K, typename TS, bool VEC, bool ALL = false>
-__global__ void __launch_bounds__(kStreamMaxThreads)
+__global__ void __launch_bounds__(kStreamMaxThreads, stream_min_blocks(R, STAR, K))
     sweep_stream_kernel(const __grid_constant__ StreamParams p) {
     constexpr int PF = stream_prefetch(K);
     constexpr int CB = 4 * (int)sizeof(TS);
@@ -791,7 +810,7 @@ __global__ void __launch_bounds__(kStreamMaxThreads)
 // engine (FP32 storage, zero rule, rows of a multiple of 4 elements): `map`
 // describes the input grid (nx x ny, row pitch ld, box kStreamTmaBox x 1).
 template <int R, bool STAR, int K>
-__global__ void __launch_bounds__(kStreamMaxThreads)
+__global__ void __launch_bounds__(kStreamMaxThreads, stream_min_blocks(R, STAR, K))
     sweep_stream_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ StreamParams p) {
     constexpr int PF = stream_prefetch(K);
     constexpr int CB = 16;

@@ -65,3 +65,15 @@ def test_rate_is_whole_job():
     import bench
     assert bench.whole_job_rate(1, 6.7e10, 1000.0) == pytest.approx(67.0)
     assert bench.whole_job_rate(4, 6.7e10, 1000.0) == pytest.approx(4 * 67.0)
+
+
+def test_reference_arm_times_a_variant_workload():
+    """--impl reference --workload heat512: the oracle on that workload, one JSON line."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "heat512", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert "512" in line["config"]["reference_sample"]
