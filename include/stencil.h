@@ -219,6 +219,17 @@ stencil_status_t stencil_run(stencil_plan_t* plan, const void* in, void* out, in
 stencil_status_t stencil_run_host(stencil_plan_t* plan, const void* in_host, void* out_host,
                                   int64_t T, stencil_stream_t stream);
 
+/*
+ * As stencil_run_host without the final synchronisation: the copy in, the T
+ * steps and the copy out are enqueued on `stream`, and out_host holds the
+ * result once the stream has reached the end of that work.  Both host buffers
+ * must stay valid until then; with pinned host memory the copies overlap work
+ * on other streams (runs of two plans on two streams pipeline each other's
+ * copies with their sweeps), pageable memory may make them synchronous.
+ */
+stencil_status_t stencil_run_host_async(stencil_plan_t* plan, const void* in_host, void* out_host,
+                                        int64_t T, stencil_stream_t stream);
+
 /* Number of kernel launches stencil_run(plan, in, out, T) makes (in != out). */
 int64_t stencil_run_launches(const stencil_plan_t* plan, int64_t T);
 

@@ -133,6 +133,16 @@ class Plan:
                                             stream), "stencil_run_host")
         return out
 
+    def run_host_async(self, x: np.ndarray, T: int, out: np.ndarray, stream: int = 0):
+        """Host in, host out, enqueued on `stream` without synchronising
+        (stencil_run_host_async): `out` holds u_T once the stream is done.
+        Both arrays must stay alive until then; pin them for overlap."""
+        if x.shape != self.shape or not x.flags["C_CONTIGUOUS"] or out.shape != self.shape:
+            raise ValueError(f"expected C-contiguous arrays of shape {self.shape}")
+        check(_capi.load().stencil_run_host_async(self._h, x.ctypes.data, out.ctypes.data, int(T), stream),
+              "stencil_run_host_async")
+        return out
+
     def status(self):
         check(_capi.load().stencil_plan_status(self._h), "stencil_plan_status")
 

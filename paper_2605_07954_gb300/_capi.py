@@ -83,6 +83,7 @@ _PROTOS = {
     "stencil_plan_set_weights": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "stencil_run": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "stencil_run_host": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "stencil_run_host_async": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "stencil_run_launches": (_i64, [_vp, _i64]),
     "stencil_plan_status": (_i32, [_vp]),
     "stencil_status_string": (ctypes.c_char_p, [_i32]),

@@ -184,7 +184,7 @@ stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const f
     }
 
     // Fixed configuration: the library's default depth and 128-thread CTAs.
-    const int kdef = radius == 1 ? 8 : (radius == 2 ? 4 : (star ? 2 : 1));
+    const int kdef = radius == 1 ? 8 : (radius == 2 ? 4 : (star ? 3 : 1));
     const int k = depth_at_most(radius, star, kdef);
     Geometry g{};
     g.H = (radius * k + 3) / 4 * 4;

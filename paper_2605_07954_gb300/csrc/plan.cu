@@ -166,12 +166,13 @@ static int stream_depth_at_most(int R, int star, int k) {
 // Default depth before any tuning: deep enough that HBM stops binding for the
 // light stencils, 1 for the 49-point box (already arithmetic-bound at k = 1).
 // These are the best measured choices for 8192^2 FP32 grids on GB300 (the
-// 13-point star: k = 2 at 4 CTAs per SM beats k = 3 and 4, which hold more
-// partial sums per thread and fit fewer CTAs).
+// 13-point star: k = 3 with its 128-register bound, 4 CTAs per SM, ties k = 2
+// at 1173 GStencil/s and moves a third less DRAM traffic; k = 4 needs more
+// registers than fit 4 CTAs).
 static int default_depth(int R, int star) {
     if (R == 1) return 8;
     if (R == 2) return 4;
-    return star ? 2 : 1;
+    return star ? 3 : 1;
 }
 
 static const int kDefaultThreads = 128;
@@ -789,8 +790,9 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
         }
     }
     const int ths[3] = {64, 128, 256};
-    float best = 1e30f;
+    float best = 1e30f, def_time = -1.f;
     int bk = p->k, bt = p->threads, btma = p->tma;
+    const int k0 = p->k, t0 = p->opt.threads > 0 ? p->opt.threads : kDefaultThreads, tma0 = p->tma;
     const double points = (double)p->ny * (double)p->nx;
     // Row loads: both the cp.async ring and the TMA-fed ring where the plan
     // allows either (load = AUTO), else the one it fixed.
@@ -810,6 +812,7 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
                 stencil_status_t s = time_launch(p, in, reps, st, &ms);
                 if (s != STENCIL_OK) return s;
                 const float per_step = ms / (float)(reps * k);
+                if (k == k0 && th == t0 && tma == tma0) def_time = per_step;
                 if (per_step < best) {
                     best = per_step;
                     bk = k;
@@ -818,6 +821,14 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
                 }
             }
         }
+    }
+    // Keep the default configuration unless a candidate beats it by more than
+    // 2 %: closer timings are within run-to-run noise, and a stable choice
+    // keeps launch counts and profiles reproducible.
+    if (def_time > 0.f && def_time <= 1.02f * best) {
+        bk = k0;
+        bt = t0;
+        btma = tma0;
     }
     p->tma = btma;
     stencil_status_t s = configure_stream(p, bk, bt, p->opt.tile_rows);
@@ -1177,8 +1188,8 @@ stencil_status_t stencil_run(stencil_plan_t* p, const void* in, void* out, int64
     return STENCIL_OK;
 }
 
-stencil_status_t stencil_run_host(stencil_plan_t* p, const void* in_host, void* out_host,
-                                  int64_t T, stencil_stream_t stream) {
+stencil_status_t stencil_run_host_async(stencil_plan_t* p, const void* in_host, void* out_host,
+                                        int64_t T, stencil_stream_t stream) {
     if (!p) return fail(STENCIL_ERR_INVALID_ARG, "plan is NULL");
     if (!in_host || !out_host) return fail(STENCIL_ERR_INVALID_ARG, "in/out is NULL");
     if (T < 0) return fail(STENCIL_ERR_INVALID_ARG, "T must be >= 0");
@@ -1202,7 +1213,14 @@ stencil_status_t stencil_run_host(stencil_plan_t* p, const void* in_host, void* 
     stencil_status_t s = stencil_run(p, p->host_in, p->host_out, T, stream);
     if (s != STENCIL_OK) return s;
     CK(cudaMemcpyAsync(out_host, p->host_out, bytes, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    return STENCIL_OK;
+}
+
+stencil_status_t stencil_run_host(stencil_plan_t* p, const void* in_host, void* out_host,
+                                  int64_t T, stencil_stream_t stream) {
+    stencil_status_t s = stencil_run_host_async(p, in_host, out_host, T, stream);
+    if (s != STENCIL_OK) return s;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
     return STENCIL_OK;
 }
 

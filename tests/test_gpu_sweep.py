@@ -354,3 +354,29 @@ def test_periodic_unaligned_depths(oracle, name):
         got = p.run(x, 12).cpu().numpy()
         p.close()
         assert rel_linf(got, ref) <= fp32_elem_tol(12, _taps(W)), k
+
+
+def test_run_host_async_on_two_streams(oracle):
+    """Two plans, each on its own stream, host buffers in and out without a
+    synchronisation per call (stencil_run_host_async): both results match the
+    FP64 oracle once the streams are done."""
+    from paper_2605_07954_gb300 import Plan
+    outs, refs = [], []
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    plans = []
+    for name, s in zip(("box9", "star13"), streams):
+        W = inputs.pattern_weights(name)
+        u0 = inputs.field(300, 400)
+        hin = torch.from_numpy(u0).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        p = Plan(300, 400, W)
+        p.run_host_async(hin.numpy(), 25, hout.numpy(), s.cuda_stream)
+        plans.append((p, hin))
+        outs.append(hout)
+        refs.append(oracle.sweep_f64(u0, W, 25))
+    for s in streams:
+        s.synchronize()
+    for (p, _), o, r in zip(plans, outs, refs):
+        p.status()
+        assert rel_l2(o.numpy(), r) <= fp32_tol(25)
+        p.close()
