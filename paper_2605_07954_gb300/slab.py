@@ -1,4 +1,4 @@
-"""Row-slab decomposition of one grid over several ranks (torch.distributed).
+"""Sharding over several ranks: row slabs of one grid, and independent grids.
 
 The paper gives each processing element one tile with a halo (Sec. IV-A) and
 swaps halos between neighbours before every step (Sec. IV-B to IV-D).  Here
@@ -36,6 +36,28 @@ def partition(ny: int, world: int) -> list[tuple[int, int]]:
         out.append((y, y + n))
         y += n
     return out
+
+
+def lpt_partition(costs, world: int) -> list[list[int]]:
+    """Independent grids over `world` ranks: longest processing time first.
+
+    Each grid (cost = its point-steps, ny * nx * T) goes, largest first, to the
+    rank with the least assigned cost so far (ties to the lower rank).  The
+    busiest rank carries at most 4/3 of the best possible maximum (Graham's
+    bound); no grid is split and no rank exchanges anything, so a batch of
+    many grids runs as one Batch per rank with no collective.  Returns the
+    grid indices of each rank in increasing order.
+    """
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
 
 
 def geometry(ny: int, nx: int, y0: int, y1: int, radius: int, boundary: str,
@@ -202,4 +224,4 @@ class SlabSweep:
             pass
 
 
-__all__ = ["partition", "geometry", "HaloExchange", "SlabSweep"]
+__all__ = ["partition", "lpt_partition", "geometry", "HaloExchange", "SlabSweep"]

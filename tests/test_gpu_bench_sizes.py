@@ -118,3 +118,29 @@ def test_large_grid_light_cone_windows(oracle, windows, name, n, T):
     p.close()
     del x, y
     torch.cuda.empty_cache()
+
+
+def test_batched_256_grids_windows(windows):
+    """The 256-grid batched workload as bench.py runs it: the stored FP64 windows
+    of its three smallest and three largest grids after 200 steps."""
+    from paper_2605_07954_gb300 import Batch
+    sides, kinds = inputs.batch_spec(256)
+    grids = []
+    for g, (sd, kind) in enumerate(zip(sides, kinds)):
+        x = torch.from_numpy(inputs.field(int(sd), int(sd), stream=10000 + g)).cuda()
+        grids.append(dict(x=x, out=torch.empty_like(x), weights=inputs.batch_grid_weights(kind, g), T=200))
+    b = Batch(grids)
+    b.run()
+    torch.cuda.synchronize()
+    b.status()
+    checked = 0
+    for g in range(256):
+        rec = windows.get(f"batch_grid{g}")
+        if rec is None:
+            continue
+        ref = np.asarray(rec["window"])
+        got = grids[g]["out"][:16, :16].cpu().numpy()
+        assert rel_l2(got, ref) <= 1e-5, (g, int(sides[g]))
+        checked += 1
+    assert checked == 6
+    b.close()

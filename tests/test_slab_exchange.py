@@ -104,3 +104,19 @@ def test_partition_and_geometry():
         slab.geometry(64, 16, 0, 8, 3, "zero", 4)
     with pytest.raises(StencilError):
         slab.geometry(64, 16, 10, 8, 1, "zero", 4)
+
+
+def test_lpt_partition_balances_the_batch():
+    """The 256-grid batch over 1..8 ranks: every grid on exactly one rank, the
+    busiest rank within Graham's 4/3 bound of the lower bound max(mean, largest)."""
+    from paper_2605_07954_gb300 import inputs, slab
+    sides, _ = inputs.batch_spec(256)
+    costs = [int(s) * int(s) * 200 for s in sides]
+    for world in (1, 2, 3, 4, 8):
+        parts = slab.lpt_partition(costs, world)
+        assert sorted(i for p in parts for i in p) == list(range(256))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        lower = max(sum(costs) / world, max(costs))
+        assert max(loads) <= 4 / 3 * lower
+    # by hand: 5 -> r0, 4 -> r1, 3 -> r1 (4 < 5), 2 -> r0 (5 < 7), 1 -> r0 (7 = 7, lower rank)
+    assert slab.lpt_partition([5, 1, 4, 2, 3], 2) == [[0, 1, 3], [2, 4]]
