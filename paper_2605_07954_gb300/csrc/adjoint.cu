@@ -10,9 +10,10 @@
 // Memory: the states u_t are recomputed, not stored: a checkpoint every s
 // steps (s = ceil(sqrt(T)) by default) is written by a temporally blocked
 // forward pass; walking the segments backwards, each segment's s states are
-// recomputed one step per launch from its checkpoint, then the adjoint steps
-// of the segment run from its last state down to its first.  Both forward
-// paths use the same per-point arithmetic, so the result does not depend on s.
+// recomputed from its checkpoint (temporally blocked launches that store every
+// time level), then the adjoint steps of the segment run from its last state
+// down to its first.  Both forward paths use the same per-point arithmetic, so
+// the result does not depend on s.
 //
 // adjoint_step_kernel fuses, for one step, the lambda update and the
 // weight-gradient products: a CTA stages a 32x64 tile of lambda_{t+1} and of
@@ -196,28 +197,49 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) grad_w[k] = sh[0];
 }
 
-// Row-streaming variant of the reverse step (used for radius 1, widths that
-// are a multiple of 4).  A warp owns a 128-column strip of kAdsRows output rows,
-// 4 adjacent columns per lane, and walks down the rows holding the last 2R+1
-// rows of lambda_{t+1} and of u_t in registers, each extended by R halo
-// columns: the neighbouring lanes' columns by shuffles, the strip's outer
-// columns loaded by lanes 0 and 31.  Rows are loaded as 16-byte chunks
-// kAdsAhead rows before their use.  Nothing goes through shared memory on the
-// way, so the loads of one warp overlap the arithmetic of the others, where
-// adjoint_step_kernel stages a whole tile before it computes.  Per output the
-// lambda update is adjoint_step_kernel's, in the same order (bit-identical
-// lambda); each thread adds its gradient products row by row, column by
-// column, then the CTA reduces them in a fixed order into its FP64 partial.
-// Measured on GB300 (Heat 4096^2): 47.3 us per reverse step against 62.3 for
-// the staged-tile step, which is issue-bound (~128 instructions per output).
-// Unrolling the whole row walk (instruction-cache misses: 69 us), holding
-// four rows in flight instead of two (more registers, fewer warps: 58 us), or
-// bringing the rows through a per-warp cp.async ring six rows ahead (79
-// registers; the backward pass 5 % slower) were slower.
+// Row-streaming variant of the reverse step (radius 1, widths a multiple of
+// 4).  A warp owns a 128-column strip of kAdsRows output rows, 4 adjacent
+// columns per lane, and walks down the rows of lambda_{t+1} holding the last
+// 2R+1 of them in registers, each extended by R columns on either side (the
+// neighbouring lanes' columns by shuffles, the strip's outer columns loaded by
+// lanes 0 and 31).  Rows arrive as 16-byte chunks kAdsAhead rows before their
+// use; nothing goes through shared memory on the way.
+//
+// The arithmetic runs as packed FP32x2 FMAs on column pairs: own pairs
+// (c0, c1), (c2, c3) and the three pairs that straddle them, (c-1, c0),
+// (c1, c2), (c3, c4), built once per row.  Every tap (dy, dx) reads the same
+// pair of the extended lambda_{t+1} row for both products of an output pair:
+//   lambda_t[o][x]   += W[dy][dx] * lambda_{t+1}[o - dy][x - dx]
+//   dL/dW[dy][dx]    += u_t[o][x] * lambda_{t+1}[o - dy][x - dx]
+// The second line is the weight gradient sum_o lambda_{t+1}[o] u_t[o + d]
+// with its terms grouped by the u_t point (o + d -> o): every (point, tap)
+// term is counted once, by the warp that owns the u_t row, and lambda_{t+1}
+// outside the grid is zero (or wrapped) as in the lambda update, so u_t is
+// read only at the warp's own points, without halo.  Per output the lambda
+// update is adjoint_step_kernel's, in the same order (bit-identical lambda);
+// each thread adds its gradient products row by row, the CTA reduces them in
+// a fixed order into its FP64 partial.
+//
+// A warp whose rows and halo columns all lie inside the grid walks without any
+// bounds or wrap logic (pointer increments, unconditional loads); warps at the
+// grid's edge take the checked path.
+//
+// Measured on GB300 (Heat 4096^2, reverse steps back to back over distinct
+// u_t): 38.4 us per step against 29-31 us for a plain kernel that reads two
+// grids and writes one; the previous form of this step (scalar FMAs, every
+// load checked, gradient per lambda point with a u_t window) took 47.3 us at
+// about 235 warp instructions per output row, this one issues about 120.  More
+// rows in flight
+// (5 or 8 ahead in registers: fewer CTAs per SM; or a per-warp shared-memory
+// ring fed by bulk copies, 5 or 8 rows ahead), 7, 22, 25, 28 or 31 rows per
+// warp, and the warps of a CTA side by side instead of stacked all measured
+// the same or slower; evict-first loads of the rows that die with the step
+// gained ~7 %.
 constexpr int kAdsWarps = 4;    // warps per CTA, stacked vertically
 constexpr int kAdsRows = 16;    // output rows per warp
 constexpr int kAdsCols = 128;   // strip width (32 lanes x 4 columns)
 constexpr int kAdsAhead = 2;    // rows loaded ahead of their use
+constexpr int kAdsHint = 1;     // L2 policy of the row loads and stores (AdsPolicy)
 
 template <int R>
 struct AdsRow {
@@ -260,93 +282,214 @@ __device__ __forceinline__ void ads_load(AdsRow<R>& a, const float* __restrict__
     }
 }
 
-// e[k] = column c - R + k of the row, k in [0, 4 + 2R).
-template <int R>
-__device__ __forceinline__ void ads_extend(const AdsRow<R>& a, float (&e)[4 + 2 * R], int lane) {
-    const float o[4] = {a.v.x, a.v.y, a.v.z, a.v.w};
+// Column pairs of one extended row (radius 1).
+struct AdsPairs {
+    float2 p0, p1;      // (c0, c1), (c2, c3)
+    float2 sm, sc, sp;  // (c-1, c0), (c1, c2), (c3, c4)
+};
+
+__device__ __forceinline__ AdsPairs ads_pairs(const AdsRow<1>& a, int lane) {
+    const float l = __shfl_up_sync(0xffffffffu, a.v.w, 1);
+    const float r = __shfl_down_sync(0xffffffffu, a.v.x, 1);
+    AdsPairs e;
+    e.p0 = make_float2(a.v.x, a.v.y);
+    e.p1 = make_float2(a.v.z, a.v.w);
+    e.sm = make_float2(lane == 0 ? a.h[0] : l, a.v.x);
+    e.sc = make_float2(a.v.y, a.v.z);
+    e.sp = make_float2(a.v.w, lane == 31 ? a.h[0] : r);
+    return e;
+}
+
+// Columns (2q + s, 2q + 1 + s) of the extended row, s in {-1, 0, 1}.
+__device__ __forceinline__ float2 ads_pick(const AdsPairs& e, int q, int s) {
+    if (q == 0) return s < 0 ? e.sm : s == 0 ? e.p0 : e.sc;
+    return s < 0 ? e.sc : s == 0 ? e.p1 : e.sp;
+}
+
+// The lambda update and gradient products of one output row o = yb + k: pair
+// q of the row's 4 columns, window slot (jj - R - dy) mod D holding lambda_{t+1}
+// row o - dy, uu = u_t row o.
+template <int D>
+__device__ __forceinline__ float4 ads_products(const AdsPairs (&win)[D], int jj, float4 uu,
+                                               const float2 (&wp)[D * D], float2 (&g)[D * D]) {
+    constexpr int R = 1;
+    const float2 U[2] = {make_float2(uu.x, uu.y), make_float2(uu.z, uu.w)};
+    float2 acc[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) e[R + j] = o[j];
+    for (int q = 0; q < 2; ++q) {
+        acc[q] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const float l = __shfl_up_sync(0xffffffffu, o[4 - R + i], 1);
-        const float r = __shfl_down_sync(0xffffffffu, o[i], 1);
-        e[i] = lane == 0 ? a.h[i] : l;
-        e[R + 4 + i] = lane == 31 ? a.h[i] : r;
+        for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                const int t = (dy + R) * D + (dx + R);
+                const float2 L = ads_pick(win[(jj - R - dy + 2 * D) % D], q, -dx);
+                acc[q] = __ffma2_rn(wp[t], L, acc[q]);
+                g[t] = __ffma2_rn(U[q], L, g[t]);
+            }
+    }
+    return make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+}
+
+// L2 eviction priorities of the reverse step's row traffic (createpolicy and
+// .L2::cache_hint, PTX ISA).  lambda_{t+1} and u_t are dead once this step has
+// read them; lambda_t is read again by the next reverse step at once and, for
+// grids up to about half the L2, can stay there if the dead rows leave first.
+// HINT 0: default policy; 1: loads evict-first; 2: loads evict-first and
+// stores evict-last; 3: stores evict-last only.
+template <int HINT>
+struct AdsPolicy {
+    unsigned long long first = 0, last = 0;
+    __device__ __forceinline__ AdsPolicy() {
+        if (HINT == 1 || HINT == 2) asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(first));
+        if (HINT >= 2) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(last));
+    }
+    __device__ __forceinline__ float4 load4(const float* p) const {
+        if (HINT == 1 || HINT == 2) {
+            float4 v;
+            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                : "l"(p), "l"(first));
+            return v;
+        }
+        return __ldg(reinterpret_cast<const float4*>(p));
+    }
+    __device__ __forceinline__ float load1(const float* p) const {
+        if (HINT == 1 || HINT == 2) {
+            float v;
+            asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(first));
+            return v;
+        }
+        return __ldg(p);
+    }
+    __device__ __forceinline__ void store4(float* p, float4 v) const {
+        if (HINT >= 2) {
+            asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                         "f"(v.z), "f"(v.w), "l"(last)
+                         : "memory");
+        } else {
+            *reinterpret_cast<float4*>(p) = v;
+        }
+    }
+};
+
+// One warp's walk over its ROWS output rows, rows in flight held in registers
+// (AHEAD rows ahead).  EDGE: rows or halo columns may fall outside the grid
+// (checked loads, wrap, skipped outputs).
+template <bool EDGE, int AHEAD, int ROWS, class POL>
+__device__ __forceinline__ void ads_walk(const float* __restrict__ lam_in, const float* __restrict__ u,
+                                         float* __restrict__ lam_out, float2 (&g)[9], int ny, int nx,
+                                         bool per, const Weights& w, int x0, int yb, int lane, const POL& pol) {
+    constexpr int R = 1, D = 3;
+    constexpr int NR = ROWS + 2 * R;  // lambda rows walked: yb - R .. yb + ROWS - 1 + R
+    constexpr int RING = AHEAD + 1;
+    constexpr int G = RING % D == 0 ? RING : D * RING;  // a group: lcm(D, RING) rows (D = 3 is prime)
+    static_assert(NR % G == 0, "ring and window indices are static within a group of rows");
+    const int c = x0 + 4 * lane;
+    const bool col_ok = c < nx;
+    const size_t snx = (size_t)nx;
+    float2 wp[D * D];  // (w, w) pairs for the packed FMAs
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) wp[k] = make_float2(w.w[k], w.w[k]);
+
+    AdsRow<1> ra[RING];  // lambda_{t+1} rows in flight, slot = walked row % RING
+    float4 ru[RING];     // u_t rows in flight, slot = (output row + 2R) % RING, i.e. the
+                         // walked row whose step uses it
+    AdsPairs win[D];     // extended lambda_{t+1} rows, slot = walked row % D
+    // interior walk: pointers to the next row to load (never formed at EDGE)
+    const float* pl = nullptr;
+    const float* ph = nullptr;
+    const float* pu = nullptr;
+    float* po = nullptr;
+    if (!EDGE) {
+        pl = lam_in + (size_t)(yb - R) * snx + c;
+        ph = lam_in + (size_t)(yb - R) * snx + (lane == 0 ? x0 - R : x0 + kAdsCols);
+        pu = u + (size_t)yb * snx + c;
+        po = lam_out + (size_t)yb * snx + c;
+    }
+    const bool hl = lane == 0 || lane == 31;
+    auto load_lam = [&](AdsRow<1>& a, int i) {  // walked row i
+        if (EDGE) {
+            ads_load<1>(a, lam_in, yb - R + i, c, x0, lane, ny, nx, per);
+        } else {
+            a.v = pol.load4(pl);
+            a.h[0] = hl ? pol.load1(ph) : 0.f;
+            pl += snx;
+            ph += snx;
+        }
+    };
+    auto load_u = [&](float4& v, int k) {  // output row yb + k
+        if (EDGE) {
+            const int y = yb + k;
+            v = y < ny && col_ok ? __ldg(reinterpret_cast<const float4*>(u + (size_t)y * snx + c))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            v = pol.load4(pu);
+            pu += snx;
+        }
+    };
+    // the rows the first AHEAD steps use (output row k is used at walked row k + 2R)
+#pragma unroll
+    for (int i = 0; i < AHEAD; ++i) {
+        load_lam(ra[i % RING], i);
+        if (i - 2 * R >= 0 && i - 2 * R < ROWS) load_u(ru[i % RING], i - 2 * R);
+    }
+    // A rolled loop over groups of rows (a fully unrolled walk overflows the
+    // instruction cache); inside a group every ring and window index is static.
+#pragma unroll 1
+    for (int s0 = 0; s0 < NR; s0 += G) {
+#pragma unroll
+        for (int jj = 0; jj < G; ++jj) {
+            const int i = s0 + jj;
+            if (i + AHEAD < NR) load_lam(ra[(jj + AHEAD) % RING], i + AHEAD);
+            const int ku = i + AHEAD - 2 * R;  // used at walked row i + AHEAD
+            if (ku >= 0 && ku < ROWS) load_u(ru[(jj + AHEAD) % RING], ku);
+            win[jj % D] = ads_pairs(ra[jj % RING], lane);
+            // output row o = yb + k, k = i - 2R; lambda_{t+1} row o - dy is walked
+            // row i - R - dy, in window slot (jj - R - dy) mod D
+            const int k = i - 2 * R, o = yb + k;
+            if (k < 0) continue;
+            if (EDGE && (o >= ny || !col_ok)) continue;
+            const float4 res = ads_products<D>(win, jj % D, ru[jj % RING], wp, g);
+            if (EDGE) {
+                *reinterpret_cast<float4*>(lam_out + (size_t)o * snx + c) = res;
+            } else {
+                pol.store4(po, res);
+                po += snx;
+            }
+        }
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kAdsWarps * 32)
+// The reverse step (radius 1; AHEAD, ROWS: see ads_walk; HINT: L2 eviction
+// priorities, see AdsPolicy).
+template <int R, int AHEAD = kAdsAhead, int ROWS = kAdsRows, int HINT = kAdsHint>
+__global__ void __launch_bounds__(kAdsWarps * 32, 5)
     adjoint_stream_kernel(const float* __restrict__ lam_in, const float* __restrict__ u,
                           float* __restrict__ lam_out, double* __restrict__ partials, int ny, int nx,
                           int periodic, Weights w, int tiles_x) {
-    constexpr int D = 2 * R + 1, E = 4 + 2 * R;
-    constexpr int NR = kAdsRows + 2 * R;  // rows walked: yb - R .. yb + kAdsRows - 1 + R
-    constexpr int RING = kAdsAhead + 1;
-    static_assert(RING == D && NR % D == 0, "ring and window indices are static within a group of D rows");
+    static_assert(R == 1, "the row-streaming reverse step is written for radius 1");
+    constexpr int D = 2 * R + 1;
     __shared__ float red[kAdsWarps][D * D];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x0 = (blockIdx.x % tiles_x) * kAdsCols;
-    const int yb = (blockIdx.x / tiles_x) * (kAdsWarps * kAdsRows) + warp * kAdsRows;
-    const int c = x0 + 4 * lane;
-    const bool per = periodic != 0;
-    const bool col_ok = c < nx;
-
-    AdsRow<R> ra[RING], rb[RING];  // loaded rows of lambda_{t+1} and u_t, ring by row index
-    float el[D][E], eu[D][E];      // extended rows, window slot = row index % D
-    float g[D * D];
+    const int yb = (blockIdx.x / tiles_x) * (kAdsWarps * ROWS) + warp * ROWS;
+    float2 g[D * D];
 #pragma unroll
-    for (int k = 0; k < D * D; ++k) g[k] = 0.f;
-#pragma unroll
-    for (int i = 0; i < kAdsAhead; ++i) {
-        ads_load<R>(ra[i], lam_in, yb - R + i, c, x0, lane, ny, nx, per);
-        ads_load<R>(rb[i], u, yb - R + i, c, x0, lane, ny, nx, per);
-    }
-    // A rolled loop over groups of D rows (a fully unrolled walk overflows the
-    // instruction cache); inside a group every ring and window index is static.
-#pragma unroll 1
-    for (int s0 = 0; s0 < NR; s0 += D) {
-#pragma unroll
-        for (int jj = 0; jj < D; ++jj) {
-            const int i = s0 + jj;
-            if (i + kAdsAhead < NR) {
-                ads_load<R>(ra[(jj + kAdsAhead) % RING], lam_in, yb - R + i + kAdsAhead, c, x0, lane, ny, nx, per);
-                ads_load<R>(rb[(jj + kAdsAhead) % RING], u, yb - R + i + kAdsAhead, c, x0, lane, ny, nx, per);
-            }
-            ads_extend<R>(ra[jj % RING], el[jj], lane);
-            ads_extend<R>(rb[jj % RING], eu[jj], lane);
-            // output row o = yb + k, k = i - 2R; window slot (k + m) % D holds grid row o - R + m
-            const int k = i - 2 * R, o = yb + k;
-            if (k < 0 || o >= ny || !col_ok) continue;
-            constexpr int B = 2 * D * D;  // keeps (jj - 2R + m) non-negative before the modulus
-            float res[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                // lambda_t[o] = sum_d W[d] lambda_{t+1}[o - d], dy-major then dx
-                float acc = 0.f;
-#pragma unroll
-                for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                    for (int dx = -R; dx <= R; ++dx)
-                        acc = fmaf(w.w[(dy + R) * D + (dx + R)], el[(B + jj - 2 * R + R - dy) % D][j + R - dx], acc);
-                res[j] = acc;
-                // dL/dW[d] += lambda_{t+1}[o] * u_t[o + d]
-                const float lp = el[(B + jj - 2 * R + R) % D][j + R];
-#pragma unroll
-                for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-                    for (int dx = -R; dx <= R; ++dx)
-                        g[(dy + R) * D + (dx + R)] =
-                            fmaf(lp, eu[(B + jj - 2 * R + R + dy) % D][j + R + dx], g[(dy + R) * D + (dx + R)]);
-            }
-            *reinterpret_cast<float4*>(lam_out + (size_t)o * (size_t)nx + c) =
-                make_float4(res[0], res[1], res[2], res[3]);
-        }
-    }
-    // Fixed-order reduction: butterfly within each warp, then the warps in order.
+    for (int k = 0; k < D * D; ++k) g[k] = make_float2(0.f, 0.f);
+    const AdsPolicy<HINT> pol;
+    // interior: the warp's rows yb - R .. yb + ROWS - 1 + R and columns
+    // x0 - R .. x0 + 127 + R lie in the grid
+    const bool interior = yb >= R && yb + ROWS + R <= ny && x0 >= R && x0 + kAdsCols + R <= nx;
+    if (interior)
+        ads_walk<false, AHEAD, ROWS>(lam_in, u, lam_out, g, ny, nx, periodic != 0, w, x0, yb, lane, pol);
+    else
+        ads_walk<true, AHEAD, ROWS>(lam_in, u, lam_out, g, ny, nx, periodic != 0, w, x0, yb, lane, pol);
+    // Fixed-order reduction: the pair halves, a butterfly within each warp,
+    // then the warps in order.
 #pragma unroll
     for (int k = 0; k < D * D; ++k) {
-        float v = g[k];
+        float v = g[k].x + g[k].y;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (lane == 0) red[warp][k] = v;
@@ -469,7 +612,7 @@ stencil_status_t stencil_adjoint(stencil_plan_t* plan, const void* u0, const voi
     cudaStream_t st = (cudaStream_t)stream;
     Weights wf{};
     plan_weights(plan, wf.w);
-    Weights wadj = wf;  // the step kernel indexes W directly; flip is in its loop
+    Weights wadj = wf;  // the step kernels index W directly; the flip is in their loops
 
     // The row-streaming step where it applies (its 16-byte row chunks need
     // nx % 4 == 0, and the buffers below are then 16-byte aligned), else the

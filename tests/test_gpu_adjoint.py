@@ -56,7 +56,7 @@ def test_gradients_match_oracle(oracle, name, boundary):
 
 
 @pytest.mark.parametrize("boundary", ["zero", "periodic"])
-@pytest.mark.parametrize("shape", [(70, 132), (5, 8), (129, 260), (64, 4)])
+@pytest.mark.parametrize("shape", [(70, 132), (5, 8), (129, 260), (64, 4), (300, 520)])
 @pytest.mark.parametrize("name", ["heat5", "box9"])
 def test_row_streamed_step_ragged_shapes(oracle, name, shape, boundary):
     """Radius 1 with widths that are a multiple of 4 takes the row-streaming
