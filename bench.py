@@ -660,6 +660,23 @@ def variant_line(args, name, world, local, steps, warmup, e2e=True):
                    "instance": "Heat 64x64, 32 steps, vs FP64 oracle gradients", "gate_rel": 1e-4}
             acc["ok"] = acc["grad_w"]["relL2"] <= 1e-4 and acc["grad_u0"]["relL2"] <= 1e-4
             p64.close()
+        # HBM bytes the pass needs per point, by phase (nothing counted twice): the
+        # forward run and the checkpoint pass at depth k move 8/k B per point-step,
+        # the segment recompute writes every state (a read per eight writes:
+        # 4.5 B per recomputed state), the reverse step reads lambda_{t+1} and u_t
+        # and writes lambda_t (12 B per point-step)
+        info = plan.info()
+        k = max(1, int(info["tb_depth"]))
+        sgm = int(np.ceil(np.sqrt(T)))
+        nseg = -(-T // sgm)
+        per_point = 8.0 / k * T + 8.0 / k * sgm * (nseg - 1) + 4.5 * (T - nseg) + 12.0 * T
+        alg_bytes = per_point * n * n
+        peaks = _peaks()[0]
+        line["roofline_hbm_effective"] = {
+            "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+            "frac": alg_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "note": f"{per_point / T:.2f} B per point-step over the whole pass: forward and checkpoint "
+                    f"passes 8/k B (k = {k}), segment recompute 4.5 B per state, reverse step 12 B"}
         line.update({
             "metric": "GStencil/s (Heat-2D FP32 forward + adjoint, 4096^2, 512 steps)",
             "value": whole_job_rate(world, units, ms), "unit": "GStencil/s", "ms_per_step": ms,

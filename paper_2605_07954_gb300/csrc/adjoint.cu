@@ -234,7 +234,12 @@ __global__ void __launch_bounds__(256)
 // ring fed by bulk copies, 5 or 8 rows ahead), 7, 22, 25, 28 or 31 rows per
 // warp, and the warps of a CTA side by side instead of stacked all measured
 // the same or slower; evict-first loads of the rows that die with the step
-// gained ~7 %.
+// gained ~7 %.  Two reverse steps per pass (lambda_{t-1} from lambda_{t+1} in
+// registers, the middle 120 of each warp's 128 columns stored: 8 B per
+// point-step instead of 12, bit-identical lambda) ran 37.2-40.3 us per step
+// against 36.8-38.1 for the single step (136 registers and 3 CTAs per SM, or
+// 128 with spills and 4): the step is bound by the latency of each warp's row
+// walk, not by the bytes it moves.
 constexpr int kAdsWarps = 4;    // warps per CTA, stacked vertically
 constexpr int kAdsRows = 16;    // output rows per warp
 constexpr int kAdsCols = 128;   // strip width (32 lanes x 4 columns)
