@@ -896,7 +896,7 @@ def main():
             for p in PATTERNS:
                 streams[p].synchronize()
         e2e_step()
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, min(args.steps, 5))
         _barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):

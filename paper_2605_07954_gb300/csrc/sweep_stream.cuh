@@ -456,7 +456,7 @@ __host__ __device__ constexpr int stream_rows_after(int R, int K) {
 // products are still added row by row (dy = -R .. R), own columns before
 // neighbour columns, so the result does not depend on the schedule or on K.
 template <int R, bool STAR, int K, typename TS, bool VEC, bool EDGE, bool TMA = false, bool ALL = false,
-          class WS>
+          bool SKIPCOL = false, class WS>
 __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws, char* ring,
                                             float* ebuf, int NT, int tid, int x0, int y0,
                                             TmaRing tma = TmaRing{}) {
@@ -477,6 +477,13 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
     bool col_in[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) col_in[e] = !mask || (c0 + e >= 0 && c0 + e < nx);
+    // SKIPCOL (16-byte chunks, edge arrays zeroed when the tile starts): a
+    // chunk outside the grid never publishes its edge columns, so its
+    // neighbours read the zeros of the edge arrays, and its own values, which
+    // nothing else reads or stores, need no mask; only rows outside the grid
+    // are masked.
+    static_assert(!SKIPCOL || VEC, "SKIPCOL needs whole 16-byte chunks");
+    const bool pub = !(EDGE && SKIPCOL && mask) || (c0 >= 0 && c0 < nx);
     const bool store_chunk = active && c0 >= x0 && c0 + 4 <= x0 + p.bx && c0 < nx;
 
     float2 acc[K][D][2];
@@ -588,8 +595,10 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
 #pragma unroll
                 for (int l = 0; l < K; ++l) {
                     float* B = bpar + 2 * l * SZ;
-                    B[tid + 1] = Pa.x;                          // column 0
-                    B[kStreamMaxThreads + 2 + tid + 1] = Pb.y;  // column 3
+                    if (pub) {
+                        B[tid + 1] = Pa.x;                          // column 0
+                        B[kStreamMaxThreads + 2 + tid + 1] = Pb.y;  // column 3
+                    }
                     own_products<R, STAR, 0, 2 * R>(ws, acc[l], Pa, Pb, j);
                     __syncthreads();
                     ExtRow<R> ext;
@@ -604,11 +613,15 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                     if constexpr (EDGE) {
                         if (mask) {
                             const int yo = ybeg - (l + 1) * R + s;
-                            const bool row_out = yo < 0 || yo >= ny;
-                            if (row_out || !col_in[0]) Pa.x = 0.f;
-                            if (row_out || !col_in[2]) Pa.y = 0.f;
-                            if (row_out || !col_in[1]) Pb.x = 0.f;
-                            if (row_out || !col_in[3]) Pb.y = 0.f;
+                            const bool row_out = (unsigned)yo >= (unsigned)ny;
+                            if constexpr (SKIPCOL) {
+                                if (row_out) Pa = Pb = make_float2(0.f, 0.f);
+                            } else {
+                                if (row_out || !col_in[0]) Pa.x = 0.f;
+                                if (row_out || !col_in[2]) Pa.y = 0.f;
+                                if (row_out || !col_in[1]) Pb.x = 0.f;
+                                if (row_out || !col_in[3]) Pb.y = 0.f;
+                            }
                         }
                     }
                     if constexpr (ALL) {
@@ -654,11 +667,13 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                 float2 Pa, Pb;
                 level_in(l, Pa, Pb);
                 if constexpr (R == 1) {
-                    B[tid + 1] = Pa.x;                          // column 0
-                    B[kStreamMaxThreads + 2 + tid + 1] = Pb.y;  // column 3
+                    if (pub) {
+                        B[tid + 1] = Pa.x;                          // column 0
+                        B[kStreamMaxThreads + 2 + tid + 1] = Pb.y;  // column 3
+                    }
                     own_products<R, STAR, 1, 2 * R>(ws, acc[l], Pa, Pb, j);
                 } else {
-                    reinterpret_cast<float4*>(B)[tid + 1] = make_float4(Pa.x, Pa.y, Pb.x, Pb.y);
+                    if (pub) reinterpret_cast<float4*>(B)[tid + 1] = make_float4(Pa.x, Pa.y, Pb.x, Pb.y);
                     own_products_adj<R, STAR, 1, 2 * R>(ws, acc[l], Pa, Pb, make_float2(Pa.y, Pb.x), j);
                 }
             }
@@ -705,16 +720,20 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                 if constexpr (EDGE) {
                     if (mask) {
                         const int yo = ybeg + s - l * (R + 1) - R;
-                        const bool row_out = yo < 0 || yo >= ny;
+                        const bool row_out = (unsigned)yo >= (unsigned)ny;
                         float2& A0 = acc[l][cdone][0];
                         float2& A1 = acc[l][cdone][1];
-                        // element e of the chunk: R == 1 (A0.x, A1.x, A0.y, A1.y),
-                        // else (A0.x, A0.y, A1.x, A1.y)
-                        constexpr int e_a0y = R == 1 ? 2 : 1, e_a1x = R == 1 ? 1 : 2;
-                        if (row_out || !col_in[0]) A0.x = 0.f;
-                        if (row_out || !col_in[e_a0y]) A0.y = 0.f;
-                        if (row_out || !col_in[e_a1x]) A1.x = 0.f;
-                        if (row_out || !col_in[3]) A1.y = 0.f;
+                        if constexpr (SKIPCOL) {
+                            if (row_out) A0 = A1 = make_float2(0.f, 0.f);
+                        } else {
+                            // element e of the chunk: R == 1 (A0.x, A1.x, A0.y, A1.y),
+                            // else (A0.x, A0.y, A1.x, A1.y)
+                            constexpr int e_a0y = R == 1 ? 2 : 1, e_a1x = R == 1 ? 1 : 2;
+                            if (row_out || !col_in[0]) A0.x = 0.f;
+                            if (row_out || !col_in[e_a0y]) A0.y = 0.f;
+                            if (row_out || !col_in[e_a1x]) A1.x = 0.f;
+                            if (row_out || !col_in[3]) A1.y = 0.f;
+                        }
                     }
                 }
                 if constexpr (ALL) {
@@ -800,10 +819,12 @@ __global__ void __launch_bounds__(kStreamMaxThreads, stream_min_blocks(R, STAR, 
     const bool interior = VEC && y0 - R * K >= 0 && ylast + stream_rows_after(R, K) <= ny &&
                           x0 - p.H >= 0 && x0 - p.H + 4 * NT <= nx;
     const ParamWeights ws{p};
+    // (edge tiles of 16-byte-chunk kernels: the edge arrays were zeroed above,
+    // so chunks outside the grid may leave them alone, SKIPCOL)
     if (interior)
         stream_tile<R, STAR, K, TS, VEC, false, false, ALL>(p, ws, ring, ebuf, NT, tid, x0, y0);
     else
-        stream_tile<R, STAR, K, TS, VEC, true, false, ALL>(p, ws, ring, ebuf, NT, tid, x0, y0);
+        stream_tile<R, STAR, K, TS, VEC, true, false, ALL, VEC>(p, ws, ring, ebuf, NT, tid, x0, y0);
 }
 
 // The same sweep with the input rows brought in by the tensor-memory-access
@@ -844,7 +865,7 @@ __global__ void __launch_bounds__(kStreamMaxThreads, stream_min_blocks(R, STAR, 
     if (interior)
         stream_tile<R, STAR, K, float, true, false, true>(p, ws, ring, ebuf, NT, tid, x0, y0, tma);
     else
-        stream_tile<R, STAR, K, float, true, true, true>(p, ws, ring, ebuf, NT, tid, x0, y0, tma);
+        stream_tile<R, STAR, K, float, true, true, true, false, true>(p, ws, ring, ebuf, NT, tid, x0, y0, tma);
 }
 
 // Host-side handle of one instantiation.
