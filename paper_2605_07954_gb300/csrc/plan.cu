@@ -175,8 +175,15 @@ static int default_depth(int R, int star) {
     return star ? 3 : 1;
 }
 
-static const int kDefaultThreads = 128;
-// Row loads before tuning where both apply: 1 = the TMA-fed ring.
+// CTA size and row feed before tuning: the configurations the autotuner keeps
+// for 8192^2 FP32 grids on GB300 (9-point box at k = 8: 64-thread CTAs, 2354
+// GStencil/s against 2256 with 128 threads and TMA rows, 2142 with 128 threads
+// and cp.async rows; 13-point star at k = 3: 128 threads, cp.async 1271).  The
+// TMA-fed ring is behind the cp.async ring elsewhere (5-point star at k = 6, 8:
+// 2772 / 2924 against 2811 / 3050; 9-point box at k = 6 with 128 threads 2012
+// against 2107; 13-point star at k = 2, 3, 4: 1060 / 1128 / 780 against 1223 /
+// 1244 / 963), so it is never the default and the autotuner times both.
+static int default_threads(int R, int star) { return (R == 1 && !star) ? 64 : 128; }
 static const int kDefaultTma = 0;
 
 // Plans whose rows the TMA-fed streaming kernel can load: FP32 storage, the
@@ -792,7 +799,7 @@ static stencil_status_t autotune(stencil_plan* p, const void* in, cudaStream_t s
     const int ths[3] = {64, 128, 256};
     float best = 1e30f, def_time = -1.f;
     int bk = p->k, bt = p->threads, btma = p->tma;
-    const int k0 = p->k, t0 = p->opt.threads > 0 ? p->opt.threads : kDefaultThreads, tma0 = p->tma;
+    const int k0 = p->k, t0 = p->opt.threads > 0 ? p->opt.threads : default_threads(p->R, p->star), tma0 = p->tma;
     const double points = (double)p->ny * (double)p->nx;
     // Row loads: both the cp.async ring and the TMA-fed ring where the plan
     // allows either (load = AUTO), else the one it fixed.
@@ -997,12 +1004,13 @@ stencil_status_t stencil_plan_create(stencil_plan_t** out, int64_t ny, int64_t n
         st = configure_naive(p);
     } else {
         const int k = o.tb_depth > 0 ? o.tb_depth : default_depth(radius, star);
-        const int threads = o.threads > 0 ? o.threads : kDefaultThreads;
+        const int threads = o.threads > 0 ? o.threads : default_threads(radius, star);
         if (o.load == STENCIL_LOAD_TMA && !tma_eligible(p))
             return bail(fail(STENCIL_ERR_UNSUPPORTED,
                              "TMA-fed rows need FP32 storage, the zero rule and nx a multiple of 4"));
+        const int k0 = std::min(k, stream_kmax(radius, star));
         p->tma = o.load == STENCIL_LOAD_TMA || (o.load == STENCIL_LOAD_AUTO && tma_eligible(p) && kDefaultTma);
-        st = configure_stream(p, std::min(k, stream_kmax(radius, star)), threads, o.tile_rows);
+        st = configure_stream(p, k0, threads, o.tile_rows);
         // Small grids: the cluster-resident kernel, unless the caller asked for
         // the streaming kernel or set one of its options.
         // With kernel = RESIDENT, tb_depth is its number of steps per halo exchange.

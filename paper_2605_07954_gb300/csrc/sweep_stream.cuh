@@ -433,6 +433,40 @@ __host__ __device__ constexpr bool stream_handover(int R) { return R >= 2; }
 // rounding the loop up to its unroll.  A tile whose rows
 // [y0 - R*K, ylast + stream_rows_after) lie in the grid needs no row bounds
 // checks.
+// The tile of CTA b in a grid of strips x tiles_y tiles.  The edge tiles (top
+// and bottom tile rows, left and right strips), which run the slower checked
+// path, come first: the block scheduler deals CTAs out to the SMs round-robin,
+// so the first ones land on distinct SMs instead of doubling up on some (the
+// launch lasts as long as its most loaded SM).  Then the interior tiles, row
+// by row.
+__device__ __forceinline__ void stream_tile_of(int b, int strips, int tiles_y, int& strip, int& tile) {
+    if (strips < 3 || tiles_y < 3) {
+        strip = b % strips;
+        tile = b / strips;
+        return;
+    }
+    const int ne = 2 * strips + 2 * (tiles_y - 2);
+    if (b < 2 * strips) {
+        strip = b % strips;
+        tile = b < strips ? 0 : tiles_y - 1;
+    } else if (b < ne) {
+        const int i = b - 2 * strips;
+        strip = (i & 1) ? strips - 1 : 0;
+        tile = 1 + (i >> 1);
+    } else {
+        const int i = b - ne;
+        strip = 1 + i % (strips - 2);
+        tile = 1 + i / (strips - 2);
+    }
+}
+
+// Edge tiles decide per group of row steps whether completed rows can lie
+// outside the grid (two copies of the group body) for radius 1; radius 2 and 3
+// check every level row (the second copy pushes the 13-point star at K = 3
+// from ~140 to 344 bytes of spills: 1249 -> 1088 GStencil/s, while the
+// 9-point box at K = 8 gains 2081 -> 2152).
+__host__ __device__ constexpr bool stream_row_gate(int R) { return R == 1; }
+
 __host__ __device__ constexpr int stream_rows_after(int R, int K) {
     return R * K + (stream_handover(R) ? K : 0) + 2 * R + 1;
 }
@@ -566,7 +600,12 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
         load_chunk_scalar<TS>(p, ybeg + 1, c0, active, nreg1);
     }
 
-    for (int s0 = 0; s0 < nsteps; s0 += D) {
+    // One group of D row steps; MR: some level row the group completes may lie
+    // outside the grid (zero rule, edge tiles), so completed rows are checked.
+    // Deciding once per group keeps the row checks out of the groups that
+    // cannot need them (a branch around whole groups, not per level row).
+    auto group = [&](int s0, auto mr) {
+        constexpr bool MR = decltype(mr)::value;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const int s = s0 + j;
@@ -610,7 +649,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                     // Output row (arriving row) - R of level l+1 is complete.
                     Pa = acc[l][cdone][0];
                     Pb = acc[l][cdone][1];
-                    if constexpr (EDGE) {
+                    if constexpr (EDGE && (MR || !SKIPCOL || !stream_row_gate(R))) {
                         if (mask) {
                             const int yo = ybeg - (l + 1) * R + s;
                             const bool row_out = (unsigned)yo >= (unsigned)ny;
@@ -717,7 +756,7 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
                     }
                 }
                 // acc[l][cdone] is level l+1's row ybeg + s - l(R+1) - R, complete.
-                if constexpr (EDGE) {
+                if constexpr (EDGE && (MR || !SKIPCOL || !stream_row_gate(R))) {
                     if (mask) {
                         const int yo = ybeg + s - l * (R + 1) - R;
                         const bool row_out = (unsigned)yo >= (unsigned)ny;
@@ -764,6 +803,17 @@ __device__ __forceinline__ void stream_tile(const StreamParams& p, const WS& ws,
             }
             }  // hand-over
         }
+    };
+    for (int s0 = 0; s0 < nsteps; s0 += D) {
+        if constexpr (EDGE && SKIPCOL && stream_row_gate(R)) {
+            // level rows completed in this group: ybeg + s0 - K(R+1) .. ybeg + s0 + D - 1
+            if (mask && (ybeg + s0 - K * (R + 1) < 0 || ybeg + s0 + D > ny))
+                group(s0, std::true_type{});
+            else
+                group(s0, std::false_type{});
+        } else {
+            group(s0, std::true_type{});
+        }
     }
     if constexpr (TMA) {
         __syncthreads();  // every thread is done with the ring before the next tile's rows arrive
@@ -804,8 +854,8 @@ __global__ void __launch_bounds__(kStreamMaxThreads, stream_min_blocks(R, STAR, 
     char* ring = reinterpret_cast<char*>(smem_f4);
     float* ebuf = reinterpret_cast<float*>(ring + (VEC ? PF * NT * CB : 0));
     const int tid = threadIdx.x;
-    const int strip = blockIdx.x % p.strips;
-    const int tile = blockIdx.x / p.strips;
+    int strip, tile;
+    stream_tile_of(blockIdx.x, p.strips, gridDim.x / p.strips, strip, tile);
     const int x0 = strip * p.bx;  // first output column of the tile
     const int y0 = tile * p.by;   // first output row of the tile
 
@@ -841,8 +891,8 @@ __global__ void __launch_bounds__(kStreamMaxThreads, stream_min_blocks(R, STAR, 
     char* ctl = ring + PF * NT * CB;
     float* ebuf = reinterpret_cast<float*>(ctl + kStreamTmaCtlBytes);
     const int tid = threadIdx.x;
-    const int strip = blockIdx.x % p.strips;
-    const int tile = blockIdx.x / p.strips;
+    int strip, tile;
+    stream_tile_of(blockIdx.x, p.strips, gridDim.x / p.strips, strip, tile);
     const int x0 = strip * p.bx;
     const int y0 = tile * p.by;
     TmaRing tma;
