@@ -340,6 +340,34 @@ def test_depth_does_not_change_bits(name, boundary, shape):
     assert not bad, (name, boundary, shape, bad)
 
 
+@pytest.mark.parametrize("name", ["heat5", "box9", "star13"])
+@pytest.mark.parametrize("boundary", ["zero", "periodic"])
+def test_tiling_does_not_change_bits(oracle, name, boundary):
+    """CTA size and tile height change which CTA runs which tile (edge tiles are
+    numbered first once there are at least 3 strips and 3 tile rows) and which
+    tiles take the checked edge path, never the per-point arithmetic: every
+    tiling gives the same bits, and they match the FP64 oracle."""
+    from paper_2605_07954_gb300 import Plan
+    W = inputs.pattern_weights(name)
+    u0 = inputs.field(200, 704)
+    x = torch.from_numpy(u0).cuda()
+    T = 13
+    outs = {}
+    for threads, tile_rows in ((64, 20), (64, 0), (128, 33), (256, 0), (32, 9)):
+        p = Plan(200, 704, W, boundary=boundary, kernel="stream", threads=threads, tile_rows=tile_rows)
+        outs[(threads, tile_rows)] = (p.run(x, T), p.info())
+        torch.cuda.synchronize()
+        p.close()
+    base_key = (64, 20)
+    base, info = outs[base_key]
+    assert info["ctas"] >= 9, info
+    for key, (y, _) in outs.items():
+        assert torch.equal(y, base), (name, boundary, key)
+    ref = oracle.sweep_f64(u0, W, T, boundary)
+    got = base.cpu().numpy()
+    assert rel_l2(got, ref) <= fp32_tol(T) and rel_linf(got, ref) <= fp32_elem_tol(T, _taps(W))
+
+
 @pytest.mark.parametrize("name", PATTERNS)
 def test_periodic_unaligned_depths(oracle, name):
     """Periodic, width not a multiple of 4: every depth matches the oracle."""
