@@ -113,6 +113,33 @@ __device__ __forceinline__ float2 wgt2(const WS& ws, int m, int dx) {
     return ws.w2(m * (2 * R + 1) + dx + R);
 }
 
+// Products with scalar FMAs (weights straight from the constant bank) instead
+// of packed FP32x2 FMAs, for footprints whose (w, w) pairs do not stay in
+// registers: a packed FMA cannot take its pair from the constant bank, and
+// reloading pairs per use runs a microbenchmark at a third of the speed of the
+// scalar form (10.4 against 36.6 TFMA/s; pairs held in registers: 31.2).  The
+// two forms round identically (a packed FMA is two FMAs).  Used for the 7x7
+// box (49 pairs): 16384^2 FP32 478 -> 509 GStencil/s, BF16 storage 469 -> 489,
+// and no spills left at k = 1; the 13-point star keeps its 7 off-axis pairs in
+// registers and is faster packed (1272 against 1217 at k = 3).
+__host__ __device__ constexpr bool stream_scalar_weights(int R, bool STAR) { return R == 3 && !STAR; }
+
+template <int R, bool STAR, class WS>
+__device__ __forceinline__ float2 wfma(const WS& ws, int m, int dx, float2 src, float2 acc) {
+    if constexpr (stream_scalar_weights(R, STAR)) return sfma2(wgt2<R>(ws, m, dx).x, src, acc);
+    else return ffma2(wgt2<R>(ws, m, dx), src, acc);
+}
+
+template <int R, bool STAR, class WS>
+__device__ __forceinline__ float2 wmul(const WS& ws, int m, int dx, float2 src) {
+    if constexpr (stream_scalar_weights(R, STAR)) {
+        const float w = wgt2<R>(ws, m, dx).x;
+        return make_float2(w * src.x, w * src.y);
+    } else {
+        return fmul2(wgt2<R>(ws, m, dx), src);
+    }
+}
+
 // ---- input loading --------------------------------------------------------------
 
 template <int BYTES>
@@ -277,10 +304,10 @@ __device__ __forceinline__ void own_products(const WS& p, float2 (&acc)[2 * R + 
                 if (c != 0 && c != 1) continue;
                 const float2 src = c == 0 ? Pa : Pb;
                 if (first) {
-                    acc[slot][q] = fmul2(wgt2<R>(p, m, dx), src);
+                    acc[slot][q] = wmul<R, STAR>(p, m, dx, src);
                     first = false;
                 } else {
-                    acc[slot][q] = ffma2(wgt2<R>(p, m, dx), src, acc[slot][q]);
+                    acc[slot][q] = wfma<R, STAR>(p, m, dx, src, acc[slot][q]);
                 }
             }
         }
@@ -304,7 +331,7 @@ __device__ __forceinline__ void halo_products(const WS& p, float2 (&acc)[2 * R +
             for (int dx = -R; dx <= R; ++dx) {
                 const int c = q + dx;
                 if (c == 0 || c == 1) continue;
-                acc[slot][q] = ffma2(wgt2<R>(p, m, dx), col.pair(c), acc[slot][q]);
+                acc[slot][q] = wfma<R, STAR>(p, m, dx, col.pair(c), acc[slot][q]);
             }
         }
     }
@@ -336,10 +363,10 @@ __device__ __forceinline__ void own_products_adj(const WS& p, float2 (&acc)[2 * 
                     continue;
                 }
                 if (first) {
-                    acc[slot][q] = fmul2(wgt2<R>(p, m, dx), src);
+                    acc[slot][q] = wmul<R, STAR>(p, m, dx, src);
                     first = false;
                 } else {
-                    acc[slot][q] = ffma2(wgt2<R>(p, m, dx), src, acc[slot][q]);
+                    acc[slot][q] = wfma<R, STAR>(p, m, dx, src, acc[slot][q]);
                 }
             }
         }
@@ -363,7 +390,7 @@ __device__ __forceinline__ void halo_products_adj(const WS& p, float2 (&acc)[2 *
                 const int c = 2 * q + dx;
                 if (c >= 0 && c + 1 <= 3) continue;
                 const float2 src = make_float2(ext[c + R], ext[c + 1 + R]);
-                acc[slot][q] = ffma2(wgt2<R>(p, m, dx), src, acc[slot][q]);
+                acc[slot][q] = wfma<R, STAR>(p, m, dx, src, acc[slot][q]);
             }
         }
     }
