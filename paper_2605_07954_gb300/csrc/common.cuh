@@ -20,8 +20,10 @@ struct Weights {
     float w[kMaxTaps];
 };
 
-// The same weights duplicated into (w, w) pairs: the packed FP32x2 FMAs take a
-// pair straight from the constant bank instead of building it in registers.
+// The same weights duplicated into (w, w) pairs for the packed FP32x2 FMAs.  A
+// packed FMA takes its pair from registers: the kernels keep the pairs they use
+// often there and read them from here once (footprints with too many weights
+// for that use scalar FMAs on the single weights instead).
 struct WeightPairs {
     float2 w2[kMaxTaps];
 };
