@@ -184,12 +184,12 @@ stencil_status_t stencil_run_noalloc(int64_t ny, int64_t nx, int radius, const f
     }
 
     // Fixed configuration: the library's default depth and CTA size (64 threads
-    // for the radius-1 box, else 128).
-    const int kdef = radius == 1 ? 8 : (radius == 2 ? 4 : (star ? 3 : 1));
+    // for the radius-1 box, 256 for the radius-3 box, else 128).
+    const int kdef = radius == 1 ? 8 : (radius == 2 ? 4 : (star ? 3 : 2));
     const int k = depth_at_most(radius, star, kdef);
     Geometry g{};
     g.H = (radius * k + 3) / 4 * 4;
-    const int threads = (radius == 1 && !star) ? 64 : 128;
+    const int threads = (radius == 1 && !star) ? 64 : ((radius == 3 && !star) ? 256 : 128);
     g.strips = (int)cdiv(nx, 4 * threads - 2 * g.H);
     g.bx = (int)(cdiv(cdiv(nx, g.strips), 4) * 4);
     g.nt = (int)(cdiv(cdiv(g.bx + 2 * g.H, 4), 32) * 32);

@@ -164,7 +164,9 @@ static int stream_depth_at_most(int R, int star, int k) {
 }
 
 // Default depth before any tuning: deep enough that HBM stops binding for the
-// light stencils, 1 for the 49-point box (already arithmetic-bound at k = 1).
+// light stencils, 2 for the 49-point box (arithmetic-bound already at k = 1;
+// at 16384^2 FP32, k = 2 with 256-thread CTAs 509 GStencil/s against 478 for
+// k = 1 with 128 threads).
 // These are the best measured choices for 8192^2 FP32 grids on GB300 (the
 // 13-point star: k = 3 with its 128-register bound, 4 CTAs per SM, ties k = 2
 // at 1173 GStencil/s and moves a third less DRAM traffic; k = 4 needs more
@@ -172,7 +174,7 @@ static int stream_depth_at_most(int R, int star, int k) {
 static int default_depth(int R, int star) {
     if (R == 1) return 8;
     if (R == 2) return 4;
-    return star ? 3 : 1;
+    return star ? 3 : 2;
 }
 
 // CTA size and row feed before tuning: the configurations the autotuner keeps
@@ -183,7 +185,10 @@ static int default_depth(int R, int star) {
 // 2772 / 2924 against 2811 / 3050; 9-point box at k = 6 with 128 threads 2012
 // against 2107; 13-point star at k = 2, 3, 4: 1060 / 1128 / 780 against 1223 /
 // 1244 / 963), so it is never the default and the autotuner times both.
-static int default_threads(int R, int star) { return (R == 1 && !star) ? 64 : 128; }
+static int default_threads(int R, int star) {
+    if (R == 1 && !star) return 64;
+    return (R == 3 && !star) ? 256 : 128;
+}
 static const int kDefaultTma = 0;
 
 // Plans whose rows the TMA-fed streaming kernel can load: FP32 storage, the
