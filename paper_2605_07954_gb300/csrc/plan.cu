@@ -695,6 +695,7 @@ stencil_status_t plan_run_states(stencil_plan_t* p, const void* in, float* const
         sp.periodic = p->boundary == STENCIL_BOUNDARY_PERIODIC;
         sp.vec = 1;
         sp.status = p->status;
+        sp.wait_ns = (long long)(p->opt.timeout_ms > 0 ? p->opt.timeout_ms : 2000) * 1000000LL;
         sp.w = p->w;
         for (int t = 0; t < kMaxTaps; ++t) sp.w2.w2[t] = make_float2(p->w.w[t], p->w.w[t]);
         for (int l = 0; l < d - 1; ++l) sp.lvl_out[l] = outs[i + l];
